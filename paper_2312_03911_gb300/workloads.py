@@ -1,0 +1,202 @@
+"""Seeded synthetic workloads (problem parameters only) and their exact evidences.
+
+This module is shared by the tests, the benchmark and the smoke check.  It holds
+no step of the sampling method: it only builds likelihood parameters (means,
+widths, precision matrices) from a seed with NumPy's PCG64 generator, and the
+closed-form evidence of each workload.  The random numbers the sampler itself
+draws come from the Philox counter stream, implemented separately by the CUDA
+library and by the oracle.
+
+Workloads (stand-ins for the paper's synthetic Gaussian tasks; the paper's own
+task parameters are not all given, Section 4.1 and Appendix G):
+  c1  d=2 isotropic Gaussian N(0, 0.1^2 I), prior U[-1,1]^2, n_live=200, at least
+      5d steps per trajectory, remaining-evidence termination at 1e-3.
+  c2  d=32 equal mixture of 4 isotropic Gaussians (sigma 0.05, means U[-0.5,0.5]),
+      prior U[-1,1]^32, n_live=1000, clustering on.
+  c3  d=128 correlated Gaussian, Sigma = Q diag(lam) Q^T, lam log-uniform in
+      [1e-3, 1e-1], mean U[-0.3,0.3], prior U[-1,1]^128, n_live=2000.
+  c4  64 independent runs of uneven d and n_live (isotropic Gaussians, 4-mixtures,
+      Rosenbrock on [-2,2]^d).
+  c5  d=512 equal mixture of 8 Gaussians sharing one precision P = Sigma^-1 built
+      as in c3, means U[-0.5,0.5], prior U[-1,1]^512, n_live=4000.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 20231206
+
+LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN = 0, 1, 2, 3, 4
+
+# Hyper-parameter defaults: Appendix C table (n_live 200, tol 0.01, min_ref 1,
+# max_ref 3) and dt_ini = 0.1 (Appendix G); the momentum noise is the
+# variance-preserving refresh with delta_p = 0.2 (noise_mode 1).  The printed
+# multiplicative form (noise_mode 0) with delta_p = 0.05 remains selectable.
+DEFAULT_CFG = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.2, tol=0.01, min_ref=1,
+                   max_ref=3, prune_after=10, termination=0, clustering=1, seed=0, run_id=0,
+                   max_iters=100000, noise_mode=1, out_lo=0.05, out_hi=0.15)
+PAPER_NOISE = dict(noise_mode=0, delta_p=0.05)
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def random_orthogonal(rng, d):
+    """Q from the QR factorisation of a standard-normal matrix, columns signed so diag(R) > 0."""
+    a = rng.standard_normal((d, d))
+    q, r = np.linalg.qr(a)
+    q = q * np.sign(np.diag(r))[None, :]
+    return q
+
+
+def dense_precision(rng, d, lam_lo=1e-3, lam_hi=1e-1):
+    """Sigma = Q diag(lam) Q^T with log-uniform lam; returns (P = Sigma^-1, Sigma, lam, Q)."""
+    q = random_orthogonal(rng, d)
+    lam = np.exp(rng.uniform(math.log(lam_lo), math.log(lam_hi), size=d))
+    sigma = (q * lam[None, :]) @ q.T
+    prec = (q * (1.0 / lam)[None, :]) @ q.T
+    prec = 0.5 * (prec + prec.T)
+    sigma = 0.5 * (sigma + sigma.T)
+    return prec, sigma, lam, q
+
+
+def workload(name: str, seed: int | None = None, **over):
+    """Return dict(spec=likelihood spec, lo, hi, cfg) for a named workload."""
+    if name == "c1":
+        d = 2
+        spec = dict(kind=LIK_ISO, d=d, means=np.zeros((1, d)), sigma=np.array([0.1]))
+        lo, hi = -np.ones(d), np.ones(d)
+        cfg = dict(DEFAULT_CFG, n_live=200, min_steps=5 * d, termination=1, tol=1e-3, clustering=0)
+        base = SEED_BASE + 1
+    elif name == "c2":
+        d, K = 32, 4
+        rng = _rng(SEED_BASE + 2 if seed is None else seed)
+        spec = dict(kind=LIK_MIX_ISO, d=d, means=rng.uniform(-0.5, 0.5, size=(K, d)),
+                    sigma=np.full(K, 0.05), log_weights=np.full(K, -math.log(K)))
+        lo, hi = -np.ones(d), np.ones(d)
+        cfg = dict(DEFAULT_CFG, n_live=1000, clustering=1)
+        base = SEED_BASE + 2
+    elif name == "c3":
+        d = 128
+        rng = _rng(SEED_BASE + 3 if seed is None else seed)
+        prec, _, _, _ = dense_precision(rng, d)
+        spec = dict(kind=LIK_DENSE, d=d, means=rng.uniform(-0.3, 0.3, size=(1, d)), precision=prec)
+        lo, hi = -np.ones(d), np.ones(d)
+        cfg = dict(DEFAULT_CFG, n_live=2000, clustering=1)
+        base = SEED_BASE + 3
+    elif name == "c5":
+        d, K = 512, 8
+        rng = _rng(SEED_BASE + 5 if seed is None else seed)
+        prec, _, _, _ = dense_precision(rng, d)
+        spec = dict(kind=LIK_DENSE_MIX, d=d, means=rng.uniform(-0.5, 0.5, size=(K, d)), precision=prec,
+                    log_weights=np.full(K, -math.log(K)))
+        lo, hi = -np.ones(d), np.ones(d)
+        cfg = dict(DEFAULT_CFG, n_live=4000, clustering=1)
+        base = SEED_BASE + 5
+    else:
+        raise KeyError(name)
+    cfg["seed"] = base
+    cfg.update(over)
+    return dict(name=name, spec=spec, lo=lo, hi=hi, cfg=cfg)
+
+
+def small_workload(kind: str, d: int, n_live: int, seed: int = 7, **over):
+    """Small cases the oracle finishes in seconds (used by parity tests)."""
+    rng = _rng(seed)
+    lo, hi = -np.ones(d), np.ones(d)
+    if kind == "iso":
+        spec = dict(kind=LIK_ISO, d=d, means=rng.uniform(-0.3, 0.3, size=(1, d)), sigma=np.array([0.1]))
+    elif kind == "mix":
+        K = 4
+        spec = dict(kind=LIK_MIX_ISO, d=d, means=rng.uniform(-0.5, 0.5, size=(K, d)),
+                    sigma=np.full(K, 0.08), log_weights=np.full(K, -math.log(K)))
+    elif kind == "dense":
+        prec, _, _, _ = dense_precision(rng, d, 1e-2, 1e-1)
+        spec = dict(kind=LIK_DENSE, d=d, means=rng.uniform(-0.3, 0.3, size=(1, d)), precision=prec)
+    elif kind == "dense_mix":
+        K = 3
+        prec, _, _, _ = dense_precision(rng, d, 1e-2, 1e-1)
+        spec = dict(kind=LIK_DENSE_MIX, d=d, means=rng.uniform(-0.5, 0.5, size=(K, d)), precision=prec,
+                    log_weights=np.full(K, -math.log(K)))
+    elif kind == "rosen":
+        spec = dict(kind=LIK_ROSEN, d=d, rosen_scale=1.0 / 20.0)
+        lo, hi = -2 * np.ones(d), 2 * np.ones(d)
+    else:
+        raise KeyError(kind)
+    cfg = dict(DEFAULT_CFG, n_live=n_live, seed=seed * 1000 + 11, clustering=0)
+    cfg.update(over)
+    return dict(name=f"{kind}{d}", spec=spec, lo=lo, hi=hi, cfg=cfg)
+
+
+def batched_runs(n_runs: int = 64, seed: int = SEED_BASE + 4):
+    """The uneven batch: d from {8..256}, n_live from {100..1000}, likelihood kind drawn per run."""
+    rng = _rng(seed)
+    runs = []
+    for r in range(n_runs):
+        d = int(rng.choice([8, 16, 32, 64, 128, 256]))
+        n_live = int(rng.choice([100, 250, 500, 1000]))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            spec = dict(kind=LIK_ISO, d=d, means=rng.uniform(-0.5, 0.5, size=(1, d)),
+                        sigma=np.array([rng.uniform(0.02, 0.2)]))
+            lo, hi = -np.ones(d), np.ones(d)
+        elif kind == 1:
+            K = 4
+            spec = dict(kind=LIK_MIX_ISO, d=d, means=rng.uniform(-0.5, 0.5, size=(K, d)),
+                        sigma=np.full(K, 0.05), log_weights=np.full(K, -math.log(K)))
+            lo, hi = -np.ones(d), np.ones(d)
+        else:
+            spec = dict(kind=LIK_ROSEN, d=d, rosen_scale=1.0 / 20.0)
+            lo, hi = -2 * np.ones(d), 2 * np.ones(d)
+        cfg = dict(DEFAULT_CFG, n_live=n_live, seed=seed, run_id=r, clustering=1)
+        runs.append(dict(name=f"c4r{r}", spec=spec, lo=lo, hi=hi, cfg=cfg))
+    return runs
+
+
+# --------------------------------------------------------------------------- #
+# Exact evidences                                                               #
+# --------------------------------------------------------------------------- #
+
+def _log_box_mass_1d(mu, s, lo, hi):
+    """log P(lo < N(mu, s^2) < hi), computed stably with erfc."""
+    a = (lo - mu) / (s * math.sqrt(2.0))
+    b = (hi - mu) / (s * math.sqrt(2.0))
+    if a > 0:  # both tails on the right
+        v = 0.5 * (math.erfc(a) - math.erfc(b))
+    elif b < 0:
+        v = 0.5 * (math.erfc(-b) - math.erfc(-a))
+    else:
+        v = 1.0 - 0.5 * math.erfc(-a) - 0.5 * math.erfc(b)
+    return math.log(v)
+
+
+def truth_logz_iso_mixture(means, sigma, log_weights, lo, hi):
+    """log Z for a mixture of normalised isotropic Gaussians under the uniform box prior:
+    log[ sum_k w_k prod_i P_k(lo_i < x_i < hi_i) ] - sum_i log(hi_i - lo_i)."""
+    means = np.atleast_2d(means)
+    K, d = means.shape
+    sigma = np.broadcast_to(np.atleast_1d(sigma), (K,))
+    lw = np.full(K, -math.log(K)) if log_weights is None else np.asarray(log_weights)
+    terms = []
+    for k in range(K):
+        t = float(lw[k])
+        for i in range(d):
+            t += _log_box_mass_1d(float(means[k, i]), float(sigma[k]), float(lo[i]), float(hi[i]))
+        terms.append(t)
+    m = max(terms)
+    return m + math.log(sum(math.exp(t - m) for t in terms)) - float(np.sum(np.log(np.asarray(hi) - np.asarray(lo))))
+
+
+def truth_logz(w) -> float | None:
+    """Closed-form log Z where one exists (isotropic Gaussians and mixtures).  For the
+    dense workloads this returns the value with the box mass set to one, which is
+    exact up to the (tiny) probability mass of the Gaussian outside the box."""
+    spec, lo, hi = w["spec"], w["lo"], w["hi"]
+    if spec["kind"] in (LIK_ISO, LIK_MIX_ISO):
+        return truth_logz_iso_mixture(spec["means"], spec["sigma"], spec.get("log_weights"), lo, hi)
+    if spec["kind"] in (LIK_DENSE, LIK_DENSE_MIX):
+        return -float(np.sum(np.log(np.asarray(hi) - np.asarray(lo))))
+    return None
