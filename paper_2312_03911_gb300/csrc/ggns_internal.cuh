@@ -1,0 +1,241 @@
+// ggns_internal.cuh -- device data layout and helpers shared by the CUDA
+// translation units of libggns (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ggns.h"
+
+namespace ggns {
+
+constexpr int CMAX = 64;        // cluster slots per run
+constexpr int KNN_K = 16;       // neighbour ranks precomputed per point for Algorithm 4
+constexpr int NLIVE_MAX = 16384;
+constexpr int KMAX_COMP = 64;   // mixture components
+constexpr int DMAX = 512;
+
+// Philox counter purposes (the fourth counter word is (iteration << 4) | purpose).
+enum Purpose : uint32_t {
+    P_INIT = 0, P_MOM = 1, P_NOISE = 2, P_RES = 3, P_CLUSTER = 4, P_START = 5, P_PRUNE = 6
+};
+
+// Walker tile: G lanes per walker, E components per lane (d <= G*E).
+struct Tile {
+    int g, e;
+};
+
+// Constant description of one run (device copy, read by every kernel).
+struct RunDesc {
+    int d, d_pad, n_live, k, kind, n_comp;
+    int n_steps, min_steps, min_ref, max_ref, prune_after, termination, clustering, noise_mode;
+    float delta_p, keep, rosen_scale, lik_const;
+    double log_tol, out_lo, out_hi, dt_init;
+    uint32_t key0, key1;
+    long max_iters;
+    // offsets (elements) into the context arenas
+    long x_off;      // live x   [n_live][d_pad]         float arena
+    long pt_off;     // per-point arrays [n_live]          (logl float / label int / order int)
+    long w_off;      // per-walker arrays [k]              (start slot, new label, walker ints)
+    long ws_off;     // walker float state [k][3 d_pad]    float arena
+    long par_off;    // likelihood parameter block         float arena
+    long dead_off;   // first dead row of this run in its arrays (0: one allocation per run)
+    long dead_cap;   // rows available in the dead arrays
+    float *dead_x;   // [dead_cap][d_pad]  (reallocated by the host as the run grows)
+    float *dead_logl;
+    double *dead_logw;
+    int *dead_label;
+    long nbr_off;    // k-NN ranks [n_live][KNN_K]         int arena
+    int tile;        // walker tile id
+    int pad_;
+};
+
+// Layout of the float parameter block of one run (offsets from par_off):
+//   lo[d_pad], hi[d_pad], means[n_comp][d_pad], comp_a[n_comp], comp_b[n_comp],
+//   precision[d][d_pad] (dense kinds), pmu[n_comp][d_pad] (dense mixture: P mu_k).
+// comp_a/comp_b: ISO kinds: a = 1/sigma^2, b = log w_k - d/2 log(2 pi sigma^2);
+//                dense kinds: a unused, b = log w_k - mu_k^T P mu_k / 2 (mixture).
+struct ParLayout {
+    long lo, hi, means, comp_a, comp_b, prec, pmu, total;
+};
+__host__ __device__ inline ParLayout par_layout(int d, int d_pad, int n_comp, int kind)
+{
+    ParLayout L;
+    long o = 0;
+    L.lo = o; o += d_pad;
+    L.hi = o; o += d_pad;
+    L.means = o; o += (long)n_comp * d_pad;
+    L.comp_a = o; o += n_comp;
+    L.comp_b = o; o += n_comp;
+    o = (o + 3) & ~3L;
+    L.prec = o;
+    if (kind == NS_LIK_DENSE_GAUSS || kind == NS_LIK_DENSE_MIX) o += (long)d * d_pad;
+    L.pmu = o;
+    if (kind == NS_LIK_DENSE_MIX) o += (long)n_comp * d_pad;
+    L.total = (o + 3) & ~3L;
+    return L;
+}
+
+// Mutable per-run state.
+struct RunState {
+    int iter, done, status, terminated;
+    int n_clusters, max_clusters, t_save, t_stop;
+    double dt, log_xl, log_xl_max, lstar;
+    long n_dead, n_like, n_steps_total, n_in, n_out;
+    unsigned int wcount[3]; // walker refill counters of the three HSS phases
+    int final_done;
+    int n_fallback;
+    double logz, logz2;
+};
+
+// FP64 cluster statistics of one run (Appendix H), log space.
+struct Stats {
+    double logZp[CMAX], logZp2[CMAX], logZXp[CMAX], logZpXp[CMAX], logXp[CMAX], logXp2[CMAX];
+    double logXX[CMAX * CMAX];
+    int n[CMAX];
+    int alive[CMAX];
+};
+
+// Device view of a context.
+struct DevCtx {
+    int n_runs;
+    const RunDesc *desc;
+    RunState *state;
+    Stats *stats;
+    float *fa;        // float arena: live x, walker float state, parameters
+    float *logl;      // [sum n_live]
+    int *label;       // [sum n_live]
+    int *order;       // [sum n_live]  ascending (logL, slot) order of the last selection
+    int *start_slot;  // [sum k]
+    int *new_label;   // [sum k]
+    int *wint;        // [sum k][8]     walker integer state
+    float *wres_logl; // [sum k]
+    int *nbr;         // [sum n_live][KNN_K]
+};
+
+// ------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        U4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+    }
+    return c;
+}
+
+__device__ __forceinline__ U4 rng_block(const RunDesc &D, uint32_t iter, uint32_t purpose, uint32_t slot,
+                                        uint32_t step, uint32_t block)
+{
+    U4 c{block, step, slot, (iter << 4) | purpose};
+    return philox4x32_10(c, D.key0, D.key1);
+}
+
+// (0,1) uniform from the top 23 bits plus one half: exact in FP32.
+__device__ __forceinline__ float u01(uint32_t r)
+{
+    return (static_cast<float>(r >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+// FP64 uniform from 52 bits plus one half.
+__device__ __forceinline__ double u01_52(uint32_t r0, uint32_t r1)
+{
+    const uint64_t m = (static_cast<uint64_t>(r0) << 20) | static_cast<uint64_t>(r1 >> 12);
+    return (static_cast<double>(m) + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+// Box-Muller pair from two words.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float rad = sqrtf(-2.0f * logf(u01(a)));
+    float s, c;
+    sincospif(2.0f * u01(b), &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// The E normals of components c0 .. c0+E-1 (c0 a multiple of E; E in {1,2,4,8,16}).
+template <int E>
+__device__ __forceinline__ void lane_normals(const RunDesc &D, uint32_t iter, uint32_t purpose, uint32_t slot,
+                                             uint32_t step, int c0, float (&z)[E])
+{
+    if constexpr (E >= 4) {
+#pragma unroll
+        for (int b = 0; b < E / 4; ++b) {
+            const U4 w = rng_block(D, iter, purpose, slot, step, static_cast<uint32_t>((c0 >> 2) + b));
+            box_muller(w.x, w.y, z[4 * b + 0], z[4 * b + 1]);
+            box_muller(w.z, w.w, z[4 * b + 2], z[4 * b + 3]);
+        }
+    } else {
+        const U4 w = rng_block(D, iter, purpose, slot, step, static_cast<uint32_t>(c0 >> 2));
+        const int off = c0 & 3;
+        float a0, a1;
+        if (off < 2) box_muller(w.x, w.y, a0, a1);
+        else box_muller(w.z, w.w, a0, a1);
+        if constexpr (E == 2) {
+            z[0] = a0;
+            z[1] = a1;
+        } else {
+            z[0] = (off & 1) ? a1 : a0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Group reductions (G lanes of one warp, all 32 lanes execute them)
+// ------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ float gsum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ int gsum_i(int v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float gmax(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Order-preserving 32-bit key of a float; NaN maps to 0 (sorts first).
+__device__ __forceinline__ uint32_t float_key(float f)
+{
+    if (f != f) return 0u;
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ double log_add(double a, double b)
+{
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    const double m = a > b ? a : b;
+    return m + log1p(exp(-fabs(a - b)));
+}
+
+}  // namespace ggns

@@ -1,0 +1,1064 @@
+// ggns_iter.cu -- per-iteration kernels that are not specialised on the
+// likelihood: lowest-likelihood selection, the FP64 evidence statistics of
+// Appendix H, spawning, k-NN cluster finding (Algorithm 4), the iteration tail
+// (step-size rule and termination of Algorithm 3), the final sweep, and the
+// component entry points built on them.
+#include <cstdio>
+
+#include "ggns_iter.cuh"
+
+namespace ggns {
+
+// ------------------------------------------------------------------------
+// Block-wide bitonic sort of npow2 64-bit keys in shared memory (ascending).
+// ------------------------------------------------------------------------
+__device__ void block_bitonic_sort(unsigned long long *keys, int npow2)
+{
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned long long a = keys[i], b = keys[ixj];
+                    const bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// Key buffer: npow2 64-bit keys, reused for the kill arrays (12 bytes per kill).
+__host__ __device__ __forceinline__ size_t key_region_bytes(int n)
+{
+    const size_t a = (size_t)next_pow2(n) * 8, b = (size_t)n * 12;
+    return ((a > b ? a : b) + 15) & ~size_t(15);
+}
+
+// ------------------------------------------------------------------------
+// Appendix H statistics for a batch of kills, in closed form.
+//
+// The kills j = 0..k-1 arrive in ascending log L order with cluster labels
+// p_j.  Because update2/8/9 only rescale by n/(n+1) and n/(n+2), the volume
+// moments after r kills of a cluster telescope:
+//     X_c -> X_c (n_c - r + 1)/(n_c + 1),
+//     X_c^2 -> X_c^2 (n_c - r + 1)(n_c - r + 2)/((n_c + 1)(n_c + 2)),
+// and every kill of cluster c receives the prior mass X_c / (n_c + 1) of the
+// statistics at the start of the batch.  Writing ZX_c = X_c zeta_c, the
+// updates update5/6/7 add to zeta a constant multiple of L_j per kill, so
+// update3 becomes a sum over ordered pairs i < j.  With l_j = exp(L_j - L_ref):
+//   S1_c = sum_{j in c} l_j,  S2_c = sum_{j in c} l_j^2,
+//   U_c  = sum_{j in c} l_j sum_{i<j, i in c} l_i,
+//   V_c  = sum_{j in c} l_j sum_{i<j} a_{c,p_i} l_i,  a_{c,c} = X2_c/((n_c+2) X_c),
+//          a_{c,q} = XX_qc/((n_q+1) X_c)   (scaled by 1/X_ref to stay in range),
+// the batch applies exactly the same moments as the sequential update0-9.
+// One CTA per run; each of the first 256 threads owns a contiguous chunk of
+// kills, chunk sums are combined with sequential (deterministic) scans.
+// ------------------------------------------------------------------------
+constexpr int EV_THREADS = 256;
+constexpr int EV_CB = 8;  // target clusters per pass
+
+struct EvScratch {
+    double buf[EV_CB][EV_THREADS];
+    double coef[EV_CB][CMAX];
+    double S1[CMAX], S2[CMAX], U[CMAX], V[CMAX];
+    int m[CMAX];
+    int alive_list[CMAX];
+    int n_alive;
+    double lref;
+    double new_logZp[CMAX], new_logZp2[CMAX], new_logZXp[CMAX], new_logZpXp[CMAX], new_logXp[CMAX],
+        new_logXp2[CMAX], dZ[CMAX], dZ2[CMAX], logw[CMAX];
+};
+
+// kL[j] (FP64 log-likelihoods, ascending) and kP[j] (labels), j < k.  Updates
+// st in place (the whole CTA calls it).  logw_of_cluster receives the log prior
+// mass per kill of each cluster.  Returns nothing; st->n and st->alive updated.
+__device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, const double *kL, const int *kP,
+                               EvScratch *E)
+{
+    const int tid = threadIdx.x;
+    if (tid < CMAX) {
+        E->m[tid] = 0;
+        E->S1[tid] = E->S2[tid] = E->U[tid] = E->V[tid] = 0.0;
+    }
+    if (tid == 0) {
+        int na = 0;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c]) E->alive_list[na++] = c;
+        E->n_alive = na;
+        // L_ref: largest finite log-likelihood of the batch
+        double lr = -INFINITY;
+        for (int j = k - 1; j >= 0; --j) {
+            if (kL[j] == kL[j] && kL[j] > -INFINITY) {
+                lr = kL[j];
+                break;
+            }
+        }
+        E->lref = lr;
+    }
+    __syncthreads();
+    for (int j = tid; j < k; j += blockDim.x) atomicAdd(&E->m[kP[j]], 1);
+    __syncthreads();
+    const double lref = E->lref;
+    const bool have_l = lref > -INFINITY && lref < INFINITY;
+    const int nA = E->n_alive;
+    // X_ref: largest cluster volume (keeps the coefficients a_{c,q} <= ~1)
+    double lxref = -INFINITY;
+    for (int a = 0; a < nA; ++a) lxref = fmax(lxref, st->logXp[E->alive_list[a]]);
+
+    const int ch = (k + EV_THREADS - 1) / EV_THREADS;
+    const int j0 = min(k, tid * ch), j1 = min(k, j0 + ch);
+    for (int pb = 0; pb < nA; pb += EV_CB) {
+        const int nb = min(EV_CB, nA - pb);
+        // coefficient table for the target clusters of this pass
+        for (int i = tid; i < EV_CB * CMAX; i += blockDim.x) {
+            const int b = i / CMAX, q = i % CMAX;
+            double v = 0.0;
+            if (b < nb && st->alive[q]) {
+                const int c = E->alive_list[pb + b];
+                double lc;
+                if (q == c) lc = st->logXp2[c] - log((double)st->n[c] + 2.0) - st->logXp[c];
+                else lc = st->logXX[q * CMAX + c] - log((double)st->n[q] + 1.0) - st->logXp[c];
+                v = exp(lc - lxref);
+            }
+            E->coef[b][q] = v;
+        }
+        __syncthreads();
+        double R[EV_CB], Vl[EV_CB], Ul[EV_CB], S1l[EV_CB], S2l[EV_CB];
+        int tgt[EV_CB];
+#pragma unroll
+        for (int b = 0; b < EV_CB; ++b) {
+            R[b] = Vl[b] = Ul[b] = S1l[b] = S2l[b] = 0.0;
+            tgt[b] = (b < nb) ? E->alive_list[pb + b] : -1;
+        }
+        if (tid < EV_THREADS) {
+            for (int j = j0; j < j1; ++j) {
+                const int q = kP[j];
+                const double l = (have_l && kL[j] == kL[j]) ? exp(kL[j] - lref) : 0.0;
+#pragma unroll
+                for (int b = 0; b < EV_CB; ++b) {
+                    if (tgt[b] == q) {
+                        Vl[b] += l * R[b];
+                        Ul[b] += l * S1l[b];
+                        S1l[b] += l;
+                        S2l[b] += l * l;
+                    }
+                    R[b] += E->coef[b][q] * l;
+                }
+            }
+        }
+        // exclusive scans over threads of R and S1 (sequential per target: deterministic)
+        for (int pass = 0; pass < 2; ++pass) {
+            if (tid < EV_THREADS) {
+#pragma unroll
+                for (int b = 0; b < EV_CB; ++b) E->buf[b][tid] = pass == 0 ? R[b] : S1l[b];
+            }
+            __syncthreads();
+            if (tid < nb) {
+                double run = 0.0;
+                for (int t2 = 0; t2 < EV_THREADS; ++t2) {
+                    const double v = E->buf[tid][t2];
+                    E->buf[tid][t2] = run;
+                    run += v;
+                }
+            }
+            __syncthreads();
+            if (tid < EV_THREADS) {
+#pragma unroll
+                for (int b = 0; b < EV_CB; ++b) {
+                    if (pass == 0) Vl[b] += S1l[b] * E->buf[b][tid];
+                    else Ul[b] += S1l[b] * E->buf[b][tid];
+                }
+            }
+            __syncthreads();
+        }
+        // reductions over threads (sequential per target)
+        for (int qty = 0; qty < 4; ++qty) {
+            if (tid < EV_THREADS) {
+#pragma unroll
+                for (int b = 0; b < EV_CB; ++b)
+                    E->buf[b][tid] = qty == 0 ? S1l[b] : (qty == 1 ? S2l[b] : (qty == 2 ? Ul[b] : Vl[b]));
+            }
+            __syncthreads();
+            if (tid < nb) {
+                double sacc = 0.0;
+                for (int t2 = 0; t2 < EV_THREADS; ++t2) sacc += E->buf[tid][t2];
+                const int c = E->alive_list[pb + tid];
+                if (qty == 0) E->S1[c] = sacc;
+                else if (qty == 1) E->S2[c] = sacc;
+                else if (qty == 2) E->U[c] = sacc;
+                else E->V[c] = sacc;
+            }
+            __syncthreads();
+        }
+    }
+    // closed-form update of every live cluster (all right-hand sides old values)
+    const double LN2 = 0.69314718055994530942;
+    if (tid < CMAX && st->alive[tid]) {
+        const int c = tid;
+        const double n = (double)st->n[c];
+        const int mc = E->m[c];
+        const double Xc = st->logXp[c], X2c = st->logXp2[c];
+        const double ln1 = log(n + 1.0), ln2 = log(n + 2.0);
+        const double lS1 = log(E->S1[c]), lS2 = log(E->S2[c]), lU = log(E->U[c]), lV = log(E->V[c]);
+        const double L = lref;
+        E->logw[c] = Xc - ln1;
+        // update0/1 summed: dZ_c = X_c S1_c e^L / (n_c + 1)
+        const double dZ = (mc > 0 && have_l) ? Xc - ln1 + lS1 + L : -INFINITY;
+        E->dZ[c] = dZ;
+        // update3 summed: 2 e^L ZX_c S1/(n+1) + 2 e^2L X_c X_ref V/(n+1) + 2 e^2L X2_c S2/((n+1)(n+2))
+        double dZ2 = -INFINITY;
+        if (mc > 0 && have_l) {
+            dZ2 = log_add(dZ2, LN2 + L + st->logZXp[c] + lS1 - ln1);
+            dZ2 = log_add(dZ2, LN2 + 2.0 * L + Xc + lxref + lV - ln1);
+            dZ2 = log_add(dZ2, LN2 + 2.0 * L + X2c + lS2 - ln1 - ln2);
+        }
+        E->dZ2[c] = dZ2;
+        // update4 summed: 2 e^L Z_cX_c S1/(n+1) + 2 e^2L X2_c (U + S2)/((n+1)(n+2))
+        double dZp2 = -INFINITY;
+        if (mc > 0 && have_l) {
+            dZp2 = log_add(dZp2, LN2 + L + st->logZpXp[c] + lS1 - ln1);
+            dZp2 = log_add(dZp2, LN2 + 2.0 * L + X2c + log_add(lU, lS2) - ln1 - ln2);
+        }
+        const double nr = n - (double)mc;  // live count after the batch
+        const double lrho = (nr > 0.0) ? log(nr + 1.0) - ln1 : -INFINITY;
+        // update5/6: ZX_c -> rho (ZX_c + e^L [X2_c S1_c/(n_c+2) + sum_{q != c} XX_qc S1_q/(n_q+1)])
+        double inner = st->logZXp[c];
+        if (have_l) {
+            if (mc > 0) inner = log_add(inner, L + X2c + lS1 - ln2);
+            for (int q = 0; q < CMAX; ++q) {
+                if (q == c || !st->alive[q] || E->m[q] == 0) continue;
+                inner = log_add(inner, L + st->logXX[q * CMAX + c] + log(E->S1[q]) - log((double)st->n[q] + 1.0));
+            }
+        }
+        E->new_logZXp[c] = (nr > 0.0) ? inner + lrho : -INFINITY;
+        // update7: Z_cX_c -> rho (Z_cX_c + e^L X2_c S1_c/(n_c+2))
+        double inner2 = st->logZpXp[c];
+        if (have_l && mc > 0) inner2 = log_add(inner2, L + X2c + lS1 - ln2);
+        E->new_logZpXp[c] = (nr > 0.0) ? inner2 + lrho : -INFINITY;
+        E->new_logZp[c] = log_add(st->logZp[c], dZ);
+        E->new_logZp2[c] = log_add(st->logZp2[c], dZp2);
+        E->new_logXp[c] = Xc + lrho;
+        E->new_logXp2[c] = (nr > 0.0) ? X2c + log(nr + 1.0) + log(nr + 2.0) - ln1 - ln2 : -INFINITY;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double z = *logZ, z2 = *logZ2;
+        for (int c = 0; c < CMAX; ++c) {
+            if (!st->alive[c]) continue;
+            z = log_add(z, E->dZ[c]);
+            z2 = log_add(z2, E->dZ2[c]);
+        }
+        *logZ = z;
+        *logZ2 = z2;
+    }
+    // update9 for the cross moments (old counts), then commit
+    for (int i = tid; i < CMAX * CMAX; i += blockDim.x) {
+        const int c = i / CMAX, q = i % CMAX;
+        if (c == q || !st->alive[c] || !st->alive[q]) continue;
+        const double nc = (double)st->n[c], nq = (double)st->n[q];
+        const double rc = nc - E->m[c], rq = nq - E->m[q];
+        if (rc <= 0.0 || rq <= 0.0) st->logXX[i] = -INFINITY;
+        else st->logXX[i] += log(rc + 1.0) - log(nc + 1.0) + log(rq + 1.0) - log(nq + 1.0);
+    }
+    __syncthreads();
+    if (tid < CMAX && st->alive[tid]) {
+        const int c = tid;
+        st->logZp[c] = E->new_logZp[c];
+        st->logZp2[c] = E->new_logZp2[c];
+        st->logZXp[c] = E->new_logZXp[c];
+        st->logZpXp[c] = E->new_logZpXp[c];
+        st->logXp[c] = E->new_logXp[c];
+        st->logXp2[c] = E->new_logXp2[c];
+        st->n[c] -= E->m[c];
+        if (st->n[c] <= 0) {
+            // Algorithm 3: a cluster without points is removed
+            st->alive[c] = 0;
+            st->n[c] = 0;
+            st->logZp[c] = st->logZp2[c] = st->logZXp[c] = st->logZpXp[c] = -INFINITY;
+            st->logXp[c] = st->logXp2[c] = -INFINITY;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < CMAX * CMAX; i += blockDim.x) {
+        const int c = i / CMAX, q = i % CMAX;
+        if (!st->alive[c] || !st->alive[q]) st->logXX[i] = -INFINITY;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------
+// Selection, statistics and spawn of one iteration (Algorithm 3), one CTA per run.
+// dynamic smem: npow2 keys (8 B) | EvScratch
+// ------------------------------------------------------------------------
+constexpr int SEL_THREADS = 1024;
+
+__device__ void select_body(DevCtx C, int r, bool final_sweep)
+{
+    extern __shared__ unsigned char sraw[];
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    Stats *st = C.stats + r;
+    const int n = D.n_live;
+    const int npow = next_pow2(n);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sraw);
+    EvScratch *E = reinterpret_cast<EvScratch *>(sraw + key_region_bytes(n));
+    __shared__ int s_abort;
+    __shared__ double s_lx[2];
+    __shared__ int s_cnt[CMAX];
+    __shared__ double s_cum[CMAX];
+    __shared__ int s_start[CMAX];
+    const int tid = threadIdx.x;
+    const float *logl = C.logl + D.pt_off;
+    const int k = final_sweep ? n : D.k;
+
+    // ---- ascending (log L, slot) order; NaN first
+    for (int i = tid; i < npow; i += blockDim.x)
+        keys[i] = (i < n) ? ((unsigned long long)float_key(logl[i]) << 32) | (unsigned)i : ~0ull;
+    __syncthreads();
+    block_bitonic_sort(keys, npow);
+    for (int i = tid; i < n; i += blockDim.x) C.order[D.pt_off + i] = (int)(keys[i] & 0xffffffffu);
+    if (tid == 0) {
+        s_abort = 0;
+        if (S->n_dead + k > D.dead_cap) {
+            S->status = NS_ERR_CAPACITY;
+            S->done = 1;
+            S->final_done = 1;
+            s_abort = 1;
+        }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    // ---- kill list in the key buffer: kL (double[k]) then kP (int[k])
+    double *kL = reinterpret_cast<double *>(keys);
+    int *kP = reinterpret_cast<int *>(kL + k);
+    int *ordr = C.order + D.pt_off;
+    // (keys are dead after `order` is written; read slots back from global)
+    __syncthreads();
+    for (int j = tid; j < k; j += blockDim.x) {
+        const int s = ordr[j];
+        kL[j] = (double)logl[s];
+        kP[j] = C.label[D.pt_off + s];
+    }
+    __syncthreads();
+    const long dbase = D.dead_off + S->n_dead;
+    evidence_batch(st, &S->logz, &S->logz2, k, kL, kP, E);
+    // dead records: log L, log prior mass, label (x rows are archived by the walkers)
+    for (int j = tid; j < k; j += blockDim.x) {
+        D.dead_logl[dbase + j] = (float)kL[j];
+        D.dead_logw[dbase + j] = E->logw[kP[j]];
+        D.dead_label[dbase + j] = kP[j];
+        if (final_sweep) {
+            // the final sweep has no walkers: archive x here
+            const int s = ordr[j];
+            const float *src = C.fa + D.x_off + (long)s * D.d_pad;
+            float *dst = D.dead_x + (dbase + j) * D.d_pad;
+            for (int e = 0; e < D.d_pad; ++e) dst[e] = src[e];
+        }
+    }
+    __syncthreads();
+    if (final_sweep) {
+        if (tid == 0) {
+            S->n_dead += k;
+            S->final_done = 1;
+            if (!(S->logz == S->logz)) S->status = NS_ERR_NUMERIC;
+        }
+        return;
+    }
+    if (tid == 0) {
+        S->lstar = kL[k - 1];
+        // XL statistic on the dead-point sequence: log X (after the kills) + L*
+        double lx = -INFINITY;
+        int na = 0;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c]) {
+                lx = log_add(lx, st->logXp[c]);
+                ++na;
+            }
+        S->log_xl = lx + kL[k - 1];
+        S->n_clusters = na;
+        s_lx[0] = -INFINITY;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c]) s_lx[0] = fmax(s_lx[0], st->logXp[c]);
+        // cumulative cluster weights Xbar_p / max Xbar in id order (FP64)
+        double cum = 0.0;
+        for (int c = 0; c < CMAX; ++c) {
+            if (st->alive[c]) cum += exp(st->logXp[c] - s_lx[0]);
+            s_cum[c] = st->alive[c] ? cum : -1.0;
+        }
+        s_lx[1] = cum;
+        // survivors of each cluster occupy [s_start[c], s_start[c] + n_c) in (label, slot) order
+        int off = 0;
+        for (int c = 0; c < CMAX; ++c) {
+            s_start[c] = off;
+            if (st->alive[c]) off += st->n[c];
+            s_cnt[c] = 0;
+        }
+        if (na == 0) {
+            S->status = NS_ERR_NUMERIC;
+            S->done = 1;
+        }
+    }
+    __syncthreads();
+    if (S->done) return;
+    // ---- survivors sorted by (label, slot)
+    for (int i = tid; i < npow; i += blockDim.x) keys[i] = ~0ull;
+    __syncthreads();
+    for (int j = tid; j < n; j += blockDim.x) {
+        if (j >= k) {
+            const int s = ordr[j];
+            keys[j] = ((unsigned long long)C.label[D.pt_off + s] << 32) | (unsigned)s;
+        }
+    }
+    __syncthreads();
+    block_bitonic_sort(keys, npow);
+    // ---- spawn: cluster ~ Xbar_p, then a uniform surviving member of it
+    const uint32_t iter = (uint32_t)S->iter;
+    for (int j = tid; j < k; j += blockDim.x) {
+        const U4 w = rng_block(D, iter, P_CLUSTER, j, 0, 0);
+        const double target = u01_52(w.x, w.y) * s_lx[1];
+        int chosen = -1, last = -1;
+        for (int c = 0; c < CMAX; ++c) {
+            if (s_cum[c] < 0.0) continue;
+            last = c;
+            if (target < s_cum[c]) {
+                chosen = c;
+                break;
+            }
+        }
+        if (chosen < 0) chosen = last;
+        const int m = st->n[chosen];
+        const U4 w2 = rng_block(D, iter, P_START, j, 0, 0);
+        const int pick = (int)(((unsigned long long)w2.x * (unsigned long long)m) >> 32);
+        const int idx = s_start[chosen] + pick;
+        const unsigned long long kk = (idx < n - k) ? keys[idx] : ~0ull;
+        int slot;
+        if (kk == ~0ull || (int)(kk >> 32) != chosen) {
+            // counts and labels disagree: never expected; record it and fall back to a survivor
+            S->status = NS_ERR_NUMERIC;
+            slot = ordr[k];
+        } else {
+            slot = (int)(kk & 0xffffffffu);
+        }
+        C.start_slot[D.w_off + j] = slot;
+        C.new_label[D.w_off + j] = chosen;
+        atomicAdd(&s_cnt[chosen], 1);
+    }
+    __syncthreads();
+    if (tid < CMAX && st->alive[tid]) st->n[tid] += s_cnt[tid];
+    if (tid == 0) {
+        S->wcount[0] = S->wcount[1] = S->wcount[2] = 0;
+        S->t_save = 0;
+        S->t_stop = 0;
+        S->n_in = 0;
+        S->n_out = 0;
+        S->n_dead += k;
+    }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_select(DevCtx C)
+{
+    const int r = blockIdx.x;
+    if (C.state[r].done) return;
+    select_body(C, r, false);
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_final(DevCtx C)
+{
+    const int r = blockIdx.x;
+    if (!C.state[r].done || C.state[r].final_done) return;
+    select_body(C, r, true);
+}
+
+size_t select_smem_bytes(int n_live_max) { return key_region_bytes(n_live_max) + sizeof(EvScratch); }
+
+// ------------------------------------------------------------------------
+// Iteration tail: step-size rule (Algorithm 3), counters, termination test.
+// ------------------------------------------------------------------------
+__global__ void k_tail(DevCtx C)
+{
+    const int r = blockIdx.x;
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done) return;
+    __shared__ float s_max[32];
+    // L_max over the live points (classic termination)
+    float m = -INFINITY;
+    for (int i = threadIdx.x; i < D.n_live; i += blockDim.x) {
+        const float v = C.logl[D.pt_off + i];
+        if (v > m) m = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_max[w]);
+    const long tot = S->n_in + S->n_out;
+    const double out_frac = tot > 0 ? (double)S->n_out / (double)tot : 0.0;
+    if (out_frac > D.out_hi) S->dt *= 0.9;
+    else if (out_frac < D.out_lo) S->dt *= 1.1;
+    S->n_like += (long)D.k * S->t_stop;
+    S->n_steps_total += (long)D.k * S->t_stop;
+    if (S->log_xl > S->log_xl_max) S->log_xl_max = S->log_xl;
+    bool stop;
+    if (D.termination == 0) {
+        stop = (S->log_xl - S->log_xl_max) < D.log_tol;
+    } else {
+        double lx = -INFINITY;
+        const Stats *st = C.stats + r;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c]) lx = log_add(lx, st->logXp[c]);
+        stop = (lx + (double)m) < D.log_tol + S->logz;
+    }
+    S->iter += 1;
+    if (S->n_clusters > S->max_clusters) S->max_clusters = S->n_clusters;
+    if (stop) {
+        S->terminated = 1;
+        S->done = 1;
+    } else if (S->iter >= D.max_iters) {
+        S->status = NS_ERR_NOT_DONE;
+        S->done = 1;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Cluster finding (Algorithm 4)
+// ------------------------------------------------------------------------
+// k-NN ranks 1..KNN_K of point i among the points with the same label, by
+// ascending (FP32 squared distance, index); the distance is accumulated in
+// coordinate order with round-to-nearest and no contraction.
+constexpr int KNN_WARPS = 8;
+constexpr int KNN_TILE = 32;
+
+__device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d)
+{
+    float s = 0.f;
+    for (int t = 0; t < d; ++t) {
+        const float df = __fsub_rn(a[t], b[t]);
+        s = __fadd_rn(s, __fmul_rn(df, df));
+    }
+    return s;
+}
+
+__device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+                         float *tile /* [KNN_TILE][d+1] */, float *xi_s /* [KNN_WARPS][d] */)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * KNN_WARPS + warp;
+    const bool act = i < n;
+    const int li = act ? label[i] : -1;
+    const bool need = act && csize[li] >= 3;
+    float *xi = xi_s + warp * d;
+    if (act)
+        for (int t = lane; t < d; t += 32) xi[t] = x[(long)i * xstride + t];
+    unsigned long long L[KNN_K];
+#pragma unroll
+    for (int q = 0; q < KNN_K; ++q) L[q] = ~0ull;
+    for (int j0 = 0; j0 < n; j0 += KNN_TILE) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < KNN_TILE * d; e += blockDim.x) {
+            const int rr = e / d, t = e % d;
+            tile[rr * (d + 1) + t] = (j0 + rr < n) ? x[(long)(j0 + rr) * xstride + t] : 0.f;
+        }
+        __syncthreads();
+        const int j = j0 + lane;
+        if (need && j < n && j != i && label[j] == li) {
+            const float s = sqdist_rn(xi, tile + lane * (d + 1), d);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j;
+            if (key < L[KNN_K - 1]) {
+                L[KNN_K - 1] = key;
+#pragma unroll
+                for (int q = KNN_K - 1; q > 0; --q) {
+                    if (L[q] < L[q - 1]) {
+                        const unsigned long long tmp = L[q];
+                        L[q] = L[q - 1];
+                        L[q - 1] = tmp;
+                    }
+                }
+            }
+        }
+    }
+    // warp merge of the 32 sorted lists
+    for (int rnk = 0; rnk < KNN_K; ++rnk) {
+        unsigned long long mn = L[0];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mn, o);
+            mn = v < mn ? v : mn;
+        }
+        if (L[0] == mn && mn != ~0ull) {
+#pragma unroll
+            for (int q = 0; q < KNN_K - 1; ++q) L[q] = L[q + 1];
+            L[KNN_K - 1] = ~0ull;
+        }
+        if (act && lane == 0) nbr[(long)i * KNN_K + rnk] = (mn == ~0ull) ? -1 : (int)(mn & 0xffffffffu);
+    }
+}
+
+__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(DevCtx C)
+{
+    extern __shared__ float ksm[];
+    const int r = blockIdx.y;
+    const RunDesc &D = C.desc[r];
+    if (C.state[r].done || !D.clustering) return;
+    const int d = D.d;
+    knn_rows(C.fa + D.x_off, D.d_pad, D.n_live, d, C.label + D.pt_off, C.stats[r].n, C.nbr + D.nbr_off * 1, ksm,
+             ksm + KNN_TILE * (d + 1));
+}
+
+size_t knn_smem_bytes(int d) { return sizeof(float) * ((size_t)KNN_TILE * (d + 1) + (size_t)KNN_WARPS * d); }
+
+// Union-find in shared memory: roots are the smallest member index.
+__device__ __forceinline__ int uf_find(volatile int *par, int x)
+{
+    for (;;) {
+        const int p = par[x];
+        if (p == x) return x;
+        const int gp = par[p];
+        if (gp != p) par[x] = gp;
+        x = p;
+    }
+}
+__device__ __forceinline__ bool uf_union(int *par, int a, int b)
+{
+    for (;;) {
+        a = uf_find(par, a);
+        b = uf_find(par, b);
+        if (a == b) return false;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicCAS(&par[b], b, a);
+        if (old == b) return true;
+        b = old;
+    }
+}
+
+// The (rank)-th neighbour of point i when the precomputed ranks are exhausted:
+// the smallest (distance, index) key above `prev` among same-label points.
+__device__ unsigned long long next_neighbour(const float *x, int xstride, int n, int d, const int *label, int i,
+                                             unsigned long long prev)
+{
+    unsigned long long best = ~0ull;
+    const int li = label[i];
+    for (int j = 0; j < n; ++j) {
+        if (j == i || label[j] != li) continue;
+        const float s = sqdist_rn(x + (long)i * xstride, x + (long)j * xstride, d);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j;
+        if (key > prev && key < best) best = key;
+    }
+    return best;
+}
+
+// Components of the k-NN graphs of every active cluster (Algorithm 4): ranks 1
+// and 2 first, then rank k = 3, 4, ... until a rank merges nothing in that
+// cluster or the ranks are exhausted (k > m - 1).  Writes comp[i] = root.
+// par: shared [n]; lastkey: global scratch [n] for ranks beyond KNN_K.
+__device__ void knn_components_block(const float *x, int xstride, int n, int d, const int *label,
+                                     const int *csize, int *active, const int *nbr, int *par,
+                                     unsigned long long *lastkey, int *s_merged, int *s_live)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) par[i] = i;
+    __syncthreads();
+    for (int rank = 1;; ++rank) {
+        if (tid < CMAX) s_merged[tid] = 0;
+        if (tid == 0) *s_live = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += blockDim.x) {
+            const int c = label[i];
+            if (!active[c] || rank > csize[c] - 1) continue;
+            int j;
+            if (rank <= KNN_K) {
+                j = nbr[(long)i * KNN_K + rank - 1];
+                if (rank == KNN_K && j >= 0) {
+                    const float s = sqdist_rn(x + (long)i * xstride, x + (long)j * xstride, d);
+                    lastkey[i] = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j;
+                }
+            } else {
+                const unsigned long long key = next_neighbour(x, xstride, n, d, label, i, lastkey[i]);
+                lastkey[i] = key;
+                j = (key == ~0ull) ? -1 : (int)(key & 0xffffffffu);
+            }
+            if (j >= 0 && uf_union(par, i, j)) s_merged[c] = 1;
+        }
+        __syncthreads();
+        if (tid < CMAX && active[tid]) {
+            // a cluster stops at the first rank k >= 3 that merges nothing (its
+            // component sizes repeat), or once its ranks are exhausted (k = m - 1)
+            const bool stop = (rank >= 3 && !s_merged[tid]) || rank >= csize[tid] - 1;
+            if (stop) active[tid] = 0;
+            else atomicAdd(s_live, 1);
+        }
+        __syncthreads();
+        const int live = *s_live;
+        __syncthreads();
+        if (live == 0) break;
+    }
+    for (int i = tid; i < n; i += blockDim.x) par[i] = uf_find(par, i);
+    __syncthreads();
+}
+
+__device__ void stats_split(Stats *st, int p, int np, const int *sz, const int *ids)
+{
+    // eqs. new0-new6; new3 for Y in {Z, X_q} over every other live cluster q
+    const double n = (double)st->n[p];
+    const double Xp = st->logXp[p], Xp2 = st->logXp2[p], Zp = st->logZp[p], Zp2 = st->logZp2[p];
+    const double ZXp = st->logZXp[p], ZpXp = st->logZpXp[p];
+    double XXold[CMAX];
+    int others[CMAX];
+    for (int q = 0; q < CMAX; ++q) {
+        XXold[q] = st->logXX[p * CMAX + q];
+        others[q] = st->alive[q] && q != p;
+    }
+    for (int i = 0; i < np; ++i) {
+        const int c = ids[i];
+        const double ni = (double)sz[i];
+        const double fi = log(ni) - log(n);
+        const double gi = log(ni) + log(ni + 1.0) - log(n) - log(n + 1.0);
+        st->alive[c] = 1;
+        st->n[c] = sz[i];
+        st->logXp[c] = fi + Xp;
+        st->logXp2[c] = gi + Xp2;
+        st->logZXp[c] = fi + ZXp;
+        st->logZp[c] = fi + Zp;
+        st->logZpXp[c] = gi + ZpXp;
+        st->logZp2[c] = gi + Zp2;
+    }
+    for (int i = 0; i < np; ++i) {
+        const int c = ids[i];
+        const double fi = log((double)sz[i]) - log(n);
+        for (int q = 0; q < CMAX; ++q) {
+            if (!others[q]) continue;
+            st->logXX[c * CMAX + q] = fi + XXold[q];
+            st->logXX[q * CMAX + c] = fi + XXold[q];
+        }
+        for (int j = 0; j < np; ++j) {
+            if (j == i) continue;
+            st->logXX[c * CMAX + ids[j]] = log((double)sz[i]) + log((double)sz[j]) - log(n) - log(n + 1.0) + Xp2;
+        }
+    }
+}
+
+constexpr int CL_THREADS = 1024;
+
+__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all)
+{
+    extern __shared__ int csm[];
+    const int r = blockIdx.x;
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done || !D.clustering) return;
+    Stats *st = C.stats + r;
+    const int n = D.n_live;
+    int *par = csm;           // [n]
+    int *cnt = csm + n;       // [n]
+    int *newid = csm + 2 * n; // [n]
+    __shared__ int s_active[CMAX], s_csize[CMAX], s_merged[CMAX], s_live[1 + CMAX], s_fail;
+    const int tid = threadIdx.x;
+    int *label = C.label + D.pt_off;
+    if (tid < CMAX) {
+        s_csize[tid] = st->alive[tid] ? st->n[tid] : 0;
+        s_active[tid] = st->alive[tid] && st->n[tid] >= 3;
+    }
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    knn_components_block(C.fa + D.x_off, D.d_pad, n, D.d, label, s_csize, s_active, C.nbr + D.nbr_off, par,
+                         lastkey_all + D.pt_off, s_merged, s_live);
+    for (int i = tid; i < n; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&cnt[par[i]], 1);
+    __syncthreads();
+    if (tid == 0) {
+        // split every cluster with several components, in ascending id order;
+        // parts ordered by their smallest member, part 0 keeps the id, the others
+        // take the lowest free ids (Algorithm 3, eqs. new0-new6)
+        int exists[CMAX];
+        for (int c = 0; c < CMAX; ++c) exists[c] = st->alive[c] && s_csize[c] >= 3;
+        for (int c = 0; c < CMAX && !s_fail; ++c) {
+            if (!exists[c]) continue;
+            int np = 0;
+            int sz[CMAX], ids[CMAX], roots[CMAX];
+            for (int i = 0; i < n && !s_fail; ++i) {
+                if (label[i] == c && par[i] == i) {
+                    if (np == CMAX) {
+                        s_fail = 1;
+                        break;
+                    }
+                    roots[np] = i;
+                    sz[np] = cnt[i];
+                    ++np;
+                }
+            }
+            if (s_fail || np <= 1) continue;
+            ids[0] = c;
+            int nxt = 0;
+            for (int pi = 1; pi < np; ++pi) {
+                while (nxt < CMAX && (st->alive[nxt] || nxt == c)) ++nxt;
+                if (nxt >= CMAX) {
+                    s_fail = 1;
+                    break;
+                }
+                ids[pi] = nxt++;
+            }
+            if (s_fail) break;
+            stats_split(st, c, np, sz, ids);
+            for (int pi = 0; pi < np; ++pi) newid[roots[pi]] = ids[pi];
+            for (int i = 0; i < n; ++i)
+                if (label[i] == c) label[i] = newid[par[i]];
+        }
+        if (s_fail) {
+            S->status = NS_ERR_CAPACITY;
+            S->done = 1;
+            S->final_done = 1;
+        }
+        int na = 0;
+        for (int c = 0; c < CMAX; ++c) na += st->alive[c];
+        S->n_clusters = na;
+        if (na > S->max_clusters) S->max_clusters = na;
+    }
+}
+
+size_t cluster_smem_bytes(int n_live_max) { return sizeof(int) * 3 * (size_t)n_live_max; }
+
+// ------------------------------------------------------------------------
+// Posterior statistics: H = sum_i p_i (log L_i - log Z), one CTA per run.
+// ------------------------------------------------------------------------
+__global__ void k_info(DevCtx C, int r, double logz, double *out)
+{
+    const RunDesc &D = C.desc[r];
+    const long n = C.state[r].n_dead;
+    __shared__ double sh[32], sp[32];
+    double h = 0.0, ps = 0.0;
+    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double ll = (double)D.dead_logl[D.dead_off + i];
+        const double lp = D.dead_logw[D.dead_off + i] + ll - logz;
+        const double p = exp(lp);
+        if (p > 0.0) {
+            h += p * (ll - logz);
+            ps += p;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        h += __shfl_xor_sync(0xffffffffu, h, o);
+        ps += __shfl_xor_sync(0xffffffffu, ps, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[threadIdx.x >> 5] = h;
+        sp[threadIdx.x >> 5] = ps;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += sh[w];
+            b += sp[w];
+        }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Component entry-point kernels
+// ------------------------------------------------------------------------
+__global__ void k_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long n)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const U4 c{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    const U4 o = philox4x32_10(c, k0, k1);
+    out[4 * i] = o.x;
+    out[4 * i + 1] = o.y;
+    out[4 * i + 2] = o.z;
+    out[4 * i + 3] = o.w;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_sort_logl(const float *logl, int n, int *order)
+{
+    extern __shared__ unsigned long long skeys[];
+    const int npow = next_pow2(n);
+    for (int i = threadIdx.x; i < npow; i += blockDim.x)
+        skeys[i] = (i < n) ? ((unsigned long long)float_key(logl[i]) << 32) | (unsigned)i : ~0ull;
+    __syncthreads();
+    block_bitonic_sort(skeys, npow);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(skeys[i] & 0xffffffffu);
+}
+
+__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn_plain(const float *x, int n, int d, const int *label,
+                                                              const int *csize, int *nbr)
+{
+    extern __shared__ float ksm[];
+    knn_rows(x, d, n, d, label, csize, nbr, ksm, ksm + KNN_TILE * (d + 1));
+}
+
+__global__ void __launch_bounds__(CL_THREADS) k_components_plain(const float *x, int n, int d, const int *label,
+                                                                 const int *csize_g, const int *nbr, int *comp,
+                                                                 unsigned long long *lastkey, int *ncomp)
+{
+    extern __shared__ int csm[];
+    __shared__ int s_active[CMAX], s_csize[CMAX], s_merged[CMAX], s_live[1 + CMAX];
+    if (threadIdx.x < CMAX) {
+        s_csize[threadIdx.x] = csize_g[threadIdx.x];
+        s_active[threadIdx.x] = csize_g[threadIdx.x] >= 3;
+    }
+    __syncthreads();
+    knn_components_block(x, d, n, d, label, s_csize, s_active, nbr, csm, lastkey, s_merged, s_live);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) comp[i] = csm[i];
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int i = 0; i < n; ++i) c += (csm[i] == i);
+        *ncomp = c;
+    }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_stats_plain(Stats *st, double *zz, int k, const double *kL,
+                                                             const int *kP, double *logw_out)
+{
+    extern __shared__ unsigned char sraw[];
+    EvScratch *E = reinterpret_cast<EvScratch *>(sraw);
+    evidence_batch(st, &zz[0], &zz[1], k, kL, kP, E);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) logw_out[j] = E->logw[kP[j]];
+}
+
+size_t evscratch_bytes() { return sizeof(EvScratch); }
+
+}  // namespace ggns
+
+// ------------------------------------------------------------------------
+// Export of weighted samples: x (FP64, unpadded) and log p_i = log w_i + log L_i - log Z.
+// ------------------------------------------------------------------------
+namespace ggns {
+
+__global__ void k_export(DevCtx C, int r, int d, int d_pad, double logz, double *x, double *logp, long n)
+{
+    const RunDesc &D = C.desc[r];
+    const long tot = n * d;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const long i = e / d, c = e % d;
+        if (x) x[e] = (double)D.dead_x[(D.dead_off + i) * d_pad + c];
+        if (c == 0 && logp) logp[i] = D.dead_logw[D.dead_off + i] + (double)D.dead_logl[D.dead_off + i] - logz;
+    }
+}
+
+__global__ void k_reduce_parts(const double *part, int n_parts, int len, double *out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int p = 0; p < n_parts; ++p) s += part[(long)p * len + i];
+        out[i] = s;
+    }
+}
+
+static cudaError_t set_max_smem(const void *fn, size_t smem)
+{
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem)
+{
+    cudaError_t e;
+    if ((e = set_max_smem((const void *)k_select, sel_smem)) != cudaSuccess) return e;
+    if ((e = set_max_smem((const void *)k_final, sel_smem)) != cudaSuccess) return e;
+    if ((e = set_max_smem((const void *)k_knn, knn_smem)) != cudaSuccess) return e;
+    return set_max_smem((const void *)k_cluster, cl_smem);
+}
+
+cudaError_t launch_select(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s)
+{
+    k_select<<<n_runs, SEL_THREADS, smem, s>>>(C);
+    return cudaGetLastError();
+}
+cudaError_t launch_final(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s)
+{
+    k_final<<<n_runs, SEL_THREADS, smem, s>>>(C);
+    return cudaGetLastError();
+}
+cudaError_t launch_tail(const DevCtx &C, int n_runs, cudaStream_t s)
+{
+    k_tail<<<n_runs, 256, 0, s>>>(C);
+    return cudaGetLastError();
+}
+cudaError_t launch_knn(const DevCtx &C, int n_runs, int max_nlive, size_t smem, cudaStream_t s)
+{
+    dim3 grid((max_nlive + KNN_WARPS - 1) / KNN_WARPS, n_runs);
+    k_knn<<<grid, KNN_WARPS * 32, smem, s>>>(C);
+    return cudaGetLastError();
+}
+cudaError_t launch_cluster(const DevCtx &C, int n_runs, unsigned long long *lastkey, size_t smem, cudaStream_t s)
+{
+    k_cluster<<<n_runs, CL_THREADS, smem, s>>>(C, lastkey);
+    return cudaGetLastError();
+}
+cudaError_t launch_info(const DevCtx &C, int r, double logz, double *out, cudaStream_t s)
+{
+    k_info<<<1, 1024, 0, s>>>(C, r, logz, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_export(const DevCtx &C, int r, int d, int d_pad, double logz, double *x, double *logp, long n,
+                          cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long blocks = (n * d + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_export<<<(int)blocks, 256, 0, s>>>(C, r, d, d_pad, logz, x, logp, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce_parts(const double *part, int n_parts, int len, double *out, cudaStream_t s)
+{
+    k_reduce_parts<<<(len + 255) / 256, 256, 0, s>>>(part, n_parts, len, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, k0, k1, out, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_sort_logl(const float *logl, int n, int *order, cudaStream_t s)
+{
+    const size_t smem = (size_t)next_pow2(n) * 8;
+    cudaError_t e = set_max_smem((const void *)k_sort_logl, smem);
+    if (e != cudaSuccess) return e;
+    k_sort_logl<<<1, SEL_THREADS, smem, s>>>(logl, n, order);
+    return cudaGetLastError();
+}
+cudaError_t launch_knn_components(const float *x, int n, int d, const int *label, const int *csize, int *nbr,
+                                  int *comp, unsigned long long *lastkey, int *ncomp, cudaStream_t s)
+{
+    const size_t ks = knn_smem_bytes(d);
+    cudaError_t e = set_max_smem((const void *)k_knn_plain, ks);
+    if (e != cudaSuccess) return e;
+    k_knn_plain<<<(n + KNN_WARPS - 1) / KNN_WARPS, KNN_WARPS * 32, ks, s>>>(x, n, d, label, csize, nbr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t cs = sizeof(int) * (size_t)n;
+    e = set_max_smem((const void *)k_components_plain, cs);
+    if (e != cudaSuccess) return e;
+    k_components_plain<<<1, CL_THREADS, cs, s>>>(x, n, d, label, csize, nbr, comp, lastkey, ncomp);
+    return cudaGetLastError();
+}
+cudaError_t launch_stats_plain(Stats *st, double *zz, int k, const double *kL, const int *kP, double *logw,
+                               cudaStream_t s)
+{
+    const size_t smem = sizeof(EvScratch);
+    cudaError_t e = set_max_smem((const void *)k_stats_plain, smem);
+    if (e != cudaSuccess) return e;
+    k_stats_plain<<<1, SEL_THREADS, smem, s>>>(st, zz, k, kL, kP, logw);
+    return cudaGetLastError();
+}
+
+}  // namespace ggns

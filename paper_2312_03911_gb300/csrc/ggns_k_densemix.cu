@@ -1,0 +1,12 @@
+// ggns_k_densemix.cu -- walker-layout kernels for likelihood kind NS_LIK_DENSE_MIX.
+#define GGNS_KIND NS_LIK_DENSE_MIX
+#define GGNS_KIND_NS kind_densemix
+#include "ggns_kind_impl.cuh"
+
+namespace ggns {
+const KindLaunch &kind_launch_densemix()
+{
+    static const KindLaunch L{kind_densemix::prior, kind_densemix::hss, kind_densemix::lik, kind_densemix::grad, kind_densemix::smem_attr};
+    return L;
+}
+}  // namespace ggns

@@ -1,0 +1,675 @@
+// ggns_kernels.cuh -- walker-layout kernels templated on the likelihood kind and
+// the walker tile (G lanes per walker, E components per lane).  Each kind is
+// instantiated in its own translation unit (ggns_k_<kind>.cu).
+#pragma once
+
+#include "ggns_internal.cuh"
+
+namespace ggns {
+
+constexpr int HSS_THREADS = 128;
+
+// Shared-memory view of a run's likelihood parameters.
+struct ParView {
+    const float *lo, *hi, *means, *a, *b, *prec, *pmu;
+};
+
+// Copy the parameter block of run D into shared memory (the precision matrix
+// only when `prec_in_smem`); returns the view.  Call by the whole CTA.
+__device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *sm, bool prec_in_smem)
+{
+    const ParLayout L = par_layout(D.d, D.d_pad, D.n_comp, D.kind);
+    const float *gp = C.fa + D.par_off;
+    const long n_small = L.prec;  // lo, hi, means, a, b
+    for (long i = threadIdx.x; i < n_small; i += blockDim.x) sm[i] = gp[i];
+    long o = n_small;
+    ParView v;
+    v.lo = sm + L.lo;
+    v.hi = sm + L.hi;
+    v.means = sm + L.means;
+    v.a = sm + L.comp_a;
+    v.b = sm + L.comp_b;
+    const long n_prec = L.pmu - L.prec;
+    if (n_prec > 0 && prec_in_smem) {
+        for (long i = threadIdx.x; i < n_prec; i += blockDim.x) sm[o + i] = gp[L.prec + i];
+        v.prec = sm + o;
+        o += n_prec;
+    } else {
+        v.prec = gp + L.prec;
+    }
+    const long n_pmu = L.total - L.pmu;
+    if (n_pmu > 0) {
+        for (long i = threadIdx.x; i < n_pmu; i += blockDim.x) sm[o + i] = gp[L.pmu + i];
+        v.pmu = sm + o;
+        o += n_pmu;
+    } else {
+        v.pmu = nullptr;
+    }
+    return v;
+}
+
+// Shared memory (floats) needed by load_params.
+__host__ __device__ inline long param_smem_floats(const RunDesc &D, bool prec_in_smem)
+{
+    const ParLayout L = par_layout(D.d, D.d_pad, D.n_comp, D.kind);
+    long n = L.prec + (L.total - L.pmu);
+    if (prec_in_smem) n += L.pmu - L.prec;
+    return n;
+}
+
+// ------------------------------------------------------------------------
+// Fused log-likelihood and score (Section 2.3: only the direction of the
+// score enters the reflection; the value decides inside/outside).
+// x, g: the E components c0 .. c0+E-1 of one walker held by this lane.
+// rbuf: per-walker shared scratch of d_pad floats (dense kinds only).
+// resp: optional responsibilities per component (for d/d mu), or nullptr.
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E],
+                                          int c0, float *rbuf, float *dmu_w)
+{
+    const int d = D.d;
+    const int dp = D.d_pad;
+    if constexpr (KIND == NS_LIK_ISO_GAUSS) {
+        const float a = P.a[0];
+        float q = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float r = (c0 + e < d) ? x[e] - P.means[c0 + e] : 0.f;
+            q = fmaf(r, r, q);
+            g[e] = -a * r;
+        }
+        q = gsum<G>(q);
+        return P.b[0] - 0.5f * a * q;
+    } else if constexpr (KIND == NS_LIK_MIX_ISO) {
+        // online log-sum-exp over components in chunks of 8 (register-resident)
+        constexpr int KC = 8;
+        const int K = D.n_comp;
+        float m = -INFINITY, s = 0.f;
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            float q[KC];
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                q[kk] = 0.f;
+                if (k0 + kk < K) {
+                    const float *mu = P.means + (long)(k0 + kk) * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        q[kk] = fmaf(r, r, q[kk]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) q[kk] = gsum<G>(q[kk]);
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                if (k0 + kk < K) {
+                    const int k = k0 + kk;
+                    const float tk = P.b[k] - 0.5f * P.a[k] * q[kk];
+                    if (tk > m) {
+                        const float sc = (m == -INFINITY) ? 0.f : expf(m - tk);
+                        s *= sc;
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc[e] *= sc;
+                        m = tk;
+                    }
+                    const float wk = expf(tk - m);
+                    s += wk;
+                    const float *mu = P.means + (long)k * dp + c0;
+                    const float ak = P.a[k];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        acc[e] = fmaf(-wk * ak, r, acc[e]);
+                    }
+                }
+            }
+        }
+        const float inv = 1.f / s;
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+        if (dmu_w) {
+            // responsibilities needed by the parameter adjoint: recompute per component
+            for (int k = 0; k < K; ++k) {
+                const float *mu = P.means + (long)k * dp + c0;
+                float qk = 0.f;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                    qk = fmaf(r, r, qk);
+                }
+                qk = gsum<G>(qk);
+                dmu_w[k] = expf(P.b[k] - 0.5f * P.a[k] * qk - m) * inv;
+            }
+        }
+        return m + logf(s);
+    } else if constexpr (KIND == NS_LIK_ROSENBROCK) {
+        const float sc = D.rosen_scale;
+        const float xn = __shfl_down_sync(0xffffffffu, x[0], 1);
+        const float xp = __shfl_up_sync(0xffffffffu, x[E - 1], 1);
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            const float nxt = (e < E - 1) ? x[(e + 1) < E ? e + 1 : e] : xn;
+            const float prv = (e > 0) ? x[e > 0 ? e - 1 : 0] : xp;
+            float ge = 0.f;
+            if (c < d - 1) {
+                const float a = nxt - x[e] * x[e];
+                const float b = 1.f - x[e];
+                s = fmaf(100.f * a, a, fmaf(b, b, s));
+                ge += -sc * (-400.f * x[e] * a - 2.f * b);
+            }
+            if (c >= 1 && c < d) {
+                const float ap = x[e] - prv * prv;
+                ge += -sc * (200.f * ap);
+            }
+            g[e] = ge;
+        }
+        s = gsum<G>(s);
+        return -sc * s;
+    } else {
+        // dense kinds: y = P v on CUDA cores, v staged through the walker's shared buffer
+        const bool mix = (KIND == NS_LIK_DENSE_MIX);
+        const int K = mix ? D.n_comp : 1;
+        // stage v = x - mu (single Gaussian) or x (mixture: P x, then subtract P mu_k)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            float v = 0.f;
+            if (c < d) v = mix ? x[e] : x[e] - P.means[c];
+            rbuf[c] = v;
+        }
+        __syncwarp();
+        float y[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = 0.f;
+        for (int j = 0; j < d; ++j) {
+            const float vj = rbuf[j];
+            const float *row = P.prec + (long)j * dp + c0;  // P symmetric: row j, columns c0..
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = fmaf(row[e], vj, y[e]);
+        }
+        __syncwarp();
+        if (!mix) {
+            float q = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float r = (c0 + e < d) ? x[e] - P.means[c0 + e] : 0.f;
+                q = fmaf(r, y[e], q);
+                g[e] = (c0 + e < d) ? -y[e] : 0.f;
+            }
+            q = gsum<G>(q);
+            if (dmu_w) dmu_w[0] = 1.f;
+            return D.lik_const - 0.5f * q;
+        }
+        float m = -INFINITY, s = 0.f;
+        float acc[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const float *mu = P.means + (long)k * dp + c0;
+            const float *pm = P.pmu + (long)k * dp + c0;
+            float q = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (c0 + e < d) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
+            }
+            q = gsum<G>(q);
+            const float tk = P.b[k] - 0.5f * q;
+            if (tk > m) {
+                const float sc = (m == -INFINITY) ? 0.f : expf(m - tk);
+                s *= sc;
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[e] *= sc;
+                m = tk;
+            }
+            const float wk = expf(tk - m);
+            s += wk;
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, (c0 + e < d) ? y[e] - pm[e] : 0.f, acc[e]);
+            if (dmu_w) dmu_w[k] = tk;
+        }
+        const float inv = 1.f / s;
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+        if (dmu_w) {
+            for (int k = 0; k < K; ++k) dmu_w[k] = expf(dmu_w[k] - m) * inv;
+        }
+        return D.lik_const + m + logf(s);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Prior draws (Algorithm 3, first step): x ~ U(box) from Philox purpose 0.
+// One walker-tile group per point.
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_prior_init(DevCtx C, const int *run_list, int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const int r = run_list[blockIdx.y];
+    const RunDesc D = C.desc[r];
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    const int groups_per_cta = HSS_THREADS / G;
+    float *rbuf = rbase + (long)grp * D.d_pad;
+    for (int base = blockIdx.x * groups_per_cta; base < D.n_live; base += gridDim.x * groups_per_cta) {
+        const int i = base + grp;
+        const bool act = i < D.n_live;
+        const int ii = act ? i : 0;
+        float x[E], g[E];
+        if constexpr (E >= 4) {
+#pragma unroll
+            for (int b = 0; b < E / 4; ++b) {
+                const U4 w = rng_block(D, 0, P_INIT, ii, 0, (c0 >> 2) + b);
+                const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = c0 + 4 * b + t;
+                    x[4 * b + t] = (c < D.d) ? fmaf(P.hi[c] - P.lo[c], u01(ws[t]), P.lo[c]) : 0.f;
+                }
+            }
+        } else {
+            const U4 w = rng_block(D, 0, P_INIT, ii, 0, c0 >> 2);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = c0 + e;
+                x[e] = (c < D.d) ? fmaf(P.hi[c] - P.lo[c], u01(ws[c & 3]), P.lo[c]) : 0.f;
+            }
+        }
+        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        if (act) {
+            float *dst = C.fa + D.x_off + (long)i * D.d_pad + c0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) dst[e] = x[e];
+            if (lig == 0) {
+                C.logl[D.pt_off + i] = ll;
+                C.label[D.pt_off + i] = 0;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Batched Hamiltonian slice sampling (Algorithm 5), one of three phases:
+//   phase 0: from the start point until the walker's own n_ref >= min_ref;
+//            t_save = max over walkers of that step (the first step at which
+//            min over walkers of n_ref >= min_ref).
+//   phase 1: until t >= t_save, n_ref >= max_ref and t >= min_steps; saving
+//            inside states from t_save on; t_stop = max over walkers.
+//   phase 2: every walker continues to t_stop (the global stop), then emits
+//            the reservoir pick into its killed slot.
+// The three phases reproduce the global loop condition of Algorithm 5 without
+// a grid-wide barrier: each walker's trajectory depends only on (seed, run,
+// iteration, slot, step), so it can be cut at any step and resumed.
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_list, int phase, int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const int r = run_list[blockIdx.y];
+    const RunDesc D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done) return;
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int gbase = lane - lig;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    float *rbuf = rbase + (long)grp * D.d_pad;
+    const int W = D.k;
+    const int dp = D.d_pad;
+    const uint32_t iter = static_cast<uint32_t>(S->iter);
+    const float dt = static_cast<float>(S->dt);
+    const float lstar = static_cast<float>(S->lstar);
+    const int t_save = (phase >= 1) ? S->t_save : 0x7fffffff;
+    const int t_stop = (phase == 2) ? S->t_stop : 0;
+    const float dlt = D.delta_p;
+    const float keep = D.keep;
+
+    float x[E], p[E], xr[E], g[E], eps[E];
+    int w = 0, t = 0, nref = 0, consec = 0, count = 0, nin = 0, nout = 0;
+    float res_ll = 0.f;
+    bool active = false, exhausted = false;
+
+    for (;;) {
+        // ---- refill a finished group with the next walker of the run
+        if (!active && !exhausted) {
+            unsigned wid = 0;
+            if (lig == 0) wid = atomicAdd(&S->wcount[phase], 1u);
+            wid = __shfl_sync(gmask, wid, gbase);
+            if (wid >= static_cast<unsigned>(W)) {
+                exhausted = true;
+            } else {
+                w = static_cast<int>(wid);
+                active = true;
+                const int s0 = C.start_slot[D.w_off + w];
+                if (phase == 0) {
+                    const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) x[e] = src[e];
+                    lane_normals<E>(D, iter, P_MOM, w, 0, c0, p);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        if (c0 + e >= D.d) p[e] = 0.f;
+                        xr[e] = x[e];
+                    }
+                    t = nref = consec = count = nin = nout = 0;
+                    res_ll = 0.f;
+                    // archive the dead point that this walker's output will replace
+                    const int ks = C.order[D.pt_off + w];
+                    const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
+                    float *ddst = D.dead_x + (D.dead_off + S->n_dead - W + w) * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) ddst[e] = ksrc[e];
+                } else {
+                    const float *ws = C.fa + D.ws_off + (long)w * 3 * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        x[e] = ws[e];
+                        p[e] = ws[dp + e];
+                        xr[e] = ws[2 * dp + e];
+                    }
+                    const int *wi = C.wint + (D.w_off + w) * 8;
+                    t = wi[0]; nref = wi[1]; consec = wi[2]; count = wi[3]; nin = wi[4]; nout = wi[5];
+                    res_ll = C.wres_logl[D.w_off + w];
+                }
+            }
+        }
+        // ---- stop test of the phase; finish the walker
+        if (active) {
+            bool stop;
+            if (phase == 0) stop = (nref >= D.min_ref) || (t >= D.n_steps);
+            else if (phase == 1) stop = (t >= t_save && nref >= D.max_ref && t >= D.min_steps) || (t >= D.n_steps);
+            else stop = (t >= t_stop);
+            if (stop) {
+                if (phase < 2) {
+                    float *ws = C.fa + D.ws_off + (long)w * 3 * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        ws[e] = x[e];
+                        ws[dp + e] = p[e];
+                        ws[2 * dp + e] = xr[e];
+                    }
+                    if (lig == 0) {
+                        int *wi = C.wint + (D.w_off + w) * 8;
+                        wi[0] = t; wi[1] = nref; wi[2] = consec; wi[3] = count; wi[4] = nin; wi[5] = nout;
+                        C.wres_logl[D.w_off + w] = res_ll;
+                        if (phase == 0) atomicMax(&S->t_save, (nref >= D.min_ref) ? t : D.n_steps + 1);
+                        else atomicMax(&S->t_stop, t);
+                    }
+                } else {
+                    // emit: a uniform pick among the saved inside states, else the start point
+                    const int slot = C.order[D.pt_off + w];
+                    float *dst = C.fa + D.x_off + (long)slot * dp + c0;
+                    float out_ll;
+                    if (count > 0) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) dst[e] = xr[e];
+                        out_ll = res_ll;
+                    } else {
+                        const int s0 = C.start_slot[D.w_off + w];
+                        const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+                        for (int e = 0; e < E; ++e) dst[e] = src[e];
+                        out_ll = C.logl[D.pt_off + s0];
+                    }
+                    if (lig == 0) {
+                        C.logl[D.pt_off + slot] = out_ll;
+                        C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(nin));
+                        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
+                        if (count == 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
+                    }
+                }
+                active = false;
+            }
+        }
+        __syncwarp();
+        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        const bool stepping = active;
+
+        // ---- one step of Algorithm 5 for every stepping walker of the warp
+        const int ts = t + 1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
+        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        int outbox = 0;
+        float nb[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            nb[e] = 0.f;
+            if (c < D.d) {
+                if (x[e] < P.lo[c]) nb[e] = -1.f;
+                else if (x[e] > P.hi[c]) nb[e] = 1.f;
+            }
+            outbox += (nb[e] != 0.f);
+        }
+        outbox = gsum_i<G>(outbox);
+        const bool outside = (outbox > 0) || !(ll > lstar);
+        float pnb = 0.f, pg = 0.f, gg = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            pnb = fmaf(p[e], nb[e], pnb);
+            pg = fmaf(p[e], g[e], pg);
+            gg = fmaf(g[e], g[e], gg);
+        }
+        pnb = gsum<G>(pnb);
+        pg = gsum<G>(pg);
+        gg = gsum<G>(gg);
+        if (stepping && outside) {
+            if (outbox > 0) {
+                // reflect off the violated prior-box faces: n = nb / sqrt(#faces)
+                const float c = 2.f * pnb / static_cast<float>(outbox);
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = fmaf(-c, nb[e], p[e]);
+            } else if (gg > 0.f && gg <= 3.0e38f) {
+                // p' = p - 2 (p.n) n with n = g / |g|
+                const float c = 2.f * pg / gg;
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = fmaf(-c, g[e], p[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = -p[e];
+            }
+        }
+        // momentum noise
+        lane_normals<E>(D, iter, P_NOISE, w, ts, c0, eps);
+        if (stepping) {
+            if (D.noise_mode == 1) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = (c0 + e < D.d) ? fmaf(keep, p[e], dlt * eps[e]) : 0.f;
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
+            }
+            nref += outside ? 1 : 0;
+            if (outside) { ++nout; ++consec; } else { ++nin; consec = 0; }
+        }
+        // trajectory preservation: size-1 reservoir over the saved inside states
+        const bool save = stepping && !outside && (ts >= t_save);
+        int acc = 0;
+        if (save && lig == 0) {
+            const U4 rw = rng_block(D, iter, P_RES, w, ts, 0);
+            acc = ((static_cast<uint64_t>(rw.x) * static_cast<uint64_t>(count + 1)) >> 32) == 0;
+        }
+        acc = __shfl_sync(0xffffffffu, acc, gbase);
+        if (save) {
+            ++count;
+            if (acc) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) xr[e] = x[e];
+                res_ll = ll;
+            }
+        }
+        // pruning: back to the start point with a fresh momentum
+        if (stepping && D.prune_after > 0 && consec >= D.prune_after) {
+            const int s0 = C.start_slot[D.w_off + w];
+            const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = src[e];
+            lane_normals<E>(D, iter, P_PRUNE, w, ts, c0, p);
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (c0 + e >= D.d) p[e] = 0.f;
+            consec = 0;
+        }
+        if (stepping) t = ts;
+    }
+}
+
+// ------------------------------------------------------------------------
+// ns_lik_forward / ns_lik_backward on caller points x[n][d] (unpadded).
+// mode 0: forward (logl, grad);  mode 1: adjoint (gx = gout * grad, gmu += ...)
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_lik_points(DevCtx C, int run, const float *xin, long n, int mode,
+                                                           float *logl, float *grad, const float *gout,
+                                                           float *gmu, int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const RunDesc D = C.desc[run];
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    const int gpc = HSS_THREADS / G;
+    float *rbuf = rbase + (long)grp * D.d_pad;
+    float resp[KMAX_COMP];
+    for (long base = (long)blockIdx.x * gpc; base < n; base += (long)gridDim.x * gpc) {
+        const long i = base + grp;
+        const bool act = i < n;
+        const long ii = act ? i : 0;
+        float x[E], g[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = (c0 + e < D.d) ? xin[ii * D.d + c0 + e] : 0.f;
+        const bool want_mu = (mode == 1) && gmu != nullptr && KIND != NS_LIK_ROSENBROCK;
+        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, want_mu ? resp : nullptr);
+        if (!act) continue;
+        if (mode == 0) {
+            if (lig == 0) logl[i] = ll;
+            if (grad) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (c0 + e < D.d) grad[i * D.d + c0 + e] = g[e];
+            }
+        } else {
+            const float go = gout[i];
+            if (grad) {
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (c0 + e < D.d) grad[i * D.d + c0 + e] = go * g[e];
+            }
+            if (want_mu) {
+                const int K = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1 : D.n_comp;
+                for (int k = 0; k < K; ++k) {
+                    const float rk = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1.f : resp[k];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int c = c0 + e;
+                        if (c >= D.d) continue;
+                        float v;
+                        if (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_MIX_ISO) {
+                            v = P.a[k] * (x[e] - P.means[(long)k * D.d_pad + c]);
+                        } else if (KIND == NS_LIK_DENSE_GAUSS) {
+                            v = -g[e];  // P (x - mu)
+                        } else {
+                            // P (x - mu_k) = P x - P mu_k; recover P x from the gradient identity
+                            // is not possible for a mixture, so recompute it row by row
+                            float y = 0.f;
+                            for (int j = 0; j < D.d; ++j) y = fmaf(P.prec[(long)j * D.d_pad + c], xin[ii * D.d + j], y);
+                            v = y - P.pmu[(long)k * D.d_pad + c];
+                        }
+                        atomicAdd(&gmu[(long)k * D.d + c], go * rk * v);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Posterior-weighted parameter gradient over the dead arena (partials).
+// part[blk][K][d] (FP64) += sum_i p_i resp_ik v_ik, p_i = exp(logw_i + logL_i - logZ).
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_grad_means(DevCtx C, int run, double logz, double *part,
+                                                           int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const RunDesc D = C.desc[run];
+    const RunState *S = C.state + run;
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    double *acc = reinterpret_cast<double *>(rbase + (long)(HSS_THREADS / G) * D.d_pad + 4);
+    acc = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(acc) + 15) & ~uintptr_t(15));
+    const int K = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1 : D.n_comp;
+    for (int i = threadIdx.x; i < K * D.d; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    const int gpc = HSS_THREADS / G;
+    float *rbuf = rbase + (long)grp * D.d_pad;
+    float resp[KMAX_COMP];
+    const long n = S->n_dead;
+    for (long base = (long)blockIdx.x * gpc; base < n; base += (long)gridDim.x * gpc) {
+        const long i = base + grp;
+        const bool act = i < n;
+        const long ii = act ? i : 0;
+        const float *src = D.dead_x + (D.dead_off + ii) * D.d_pad + c0;
+        float x[E], g[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = src[e];
+        lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, resp);
+        if (!act) continue;
+        const double lp = D.dead_off >= 0 ? (D.dead_logw[D.dead_off + ii] + (double)D.dead_logl[D.dead_off + ii] - logz)
+                                          : -INFINITY;
+        const double pw = exp(lp);
+        if (!(pw > 0.0)) continue;
+        for (int k = 0; k < K; ++k) {
+            const float rk = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1.f : resp[k];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = c0 + e;
+                if (c >= D.d) continue;
+                float v;
+                if (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_MIX_ISO) {
+                    v = P.a[k] * (x[e] - P.means[(long)k * D.d_pad + c]);
+                } else if (KIND == NS_LIK_DENSE_GAUSS) {
+                    v = -g[e];
+                } else {
+                    float y = 0.f;
+                    for (int j = 0; j < D.d; ++j) y = fmaf(P.prec[(long)j * D.d_pad + c], D.dead_x[(D.dead_off + ii) * D.d_pad + j], y);
+                    v = y - P.pmu[(long)k * D.d_pad + c];
+                }
+                atomicAdd(&acc[k * D.d + c], pw * (double)rk * (double)v);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < K * D.d; i += blockDim.x) part[(long)blockIdx.x * K * D.d + i] = acc[i];
+}
+
+}  // namespace ggns

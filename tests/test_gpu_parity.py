@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer work (Philox words, orderings, cluster labels) must match bit for bit;
+FP32 arithmetic within the tolerances stated per test; full runs statistically.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_03911_gb300 import ggns
+from paper_2312_03911_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03911_gb300 import build
+    build.build()
+    ggns.load()
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+# ---------------------------------------------------------------- Philox words
+def test_philox_words_bit_exact():
+    rng = np.random.default_rng(0)
+    n = 5000
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]]
+    keys = [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xA4093822, 0x299F31D0)]
+    for k0, k1 in keys:
+        c = _dev(ctr.view(np.int32), torch.int32)
+        out = torch.zeros((n, 4), dtype=torch.int32, device="cuda")
+        ggns.philox(c.data_ptr(), k0, k1, out.data_ptr(), n)
+        got = out.cpu().numpy().view(np.uint32)
+        for i in list(range(3)) + list(rng.integers(3, n, 200)):
+            assert list(got[i]) == oracle.philox(ctr[i], [k0, k1])
+
+
+# ---------------------------------------------------------------- ordering
+@pytest.mark.parametrize("n", [1, 7, 200, 1000, 4097])
+def test_sort_order_bit_exact(n):
+    rng = np.random.default_rng(n)
+    v = rng.normal(size=n).astype(np.float32)
+    if n > 10:
+        v[rng.integers(0, n, n // 10)] = v[0]        # ties
+        v[rng.integers(0, n, 3)] = np.nan
+        v[rng.integers(0, n, 2)] = -np.inf
+    d = _dev(v, torch.float32)
+    o = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ggns.sort_logl(d.data_ptr(), n, o.data_ptr())
+    np.testing.assert_array_equal(o.cpu().numpy(), oracle.sort_by_logl(v.astype(np.float64)))
+
+
+# ---------------------------------------------------------------- clustering
+@pytest.mark.parametrize("seed,m,d,k", [(1, 60, 3, 3), (2, 300, 8, 4), (3, 1000, 32, 4), (4, 40, 2, 1),
+                                        (5, 130, 16, 2), (6, 3, 2, 1)])
+def test_knn_components_bit_exact(seed, m, d, k):
+    rng = np.random.default_rng(seed)
+    centers = rng.uniform(-1, 1, (k, d))
+    x = (centers[rng.integers(0, k, m)] + 0.08 * rng.standard_normal((m, d))).astype(np.float32)
+    xd = _dev(x, torch.float32)
+    comp = torch.zeros(m, dtype=torch.int32, device="cuda")
+    nc = ggns.knn_components(xd.data_ptr(), m, d, comp.data_ptr())
+    n_ref, comp_ref = oracle.knn_components(x)
+    assert nc == n_ref
+    np.testing.assert_array_equal(comp.cpu().numpy(), comp_ref)
+
+
+def test_knn_components_lattice_ties():
+    g = np.array([[i, j] for i in range(6) for j in range(6)], np.float32)
+    x = np.concatenate([g, g + 20.0, g * 0.5 - 30.0]).astype(np.float32)
+    xd = _dev(x, torch.float32)
+    comp = torch.zeros(len(x), dtype=torch.int32, device="cuda")
+    nc = ggns.knn_components(xd.data_ptr(), len(x), 2, comp.data_ptr())
+    n_ref, comp_ref = oracle.knn_components(x)
+    assert nc == n_ref
+    np.testing.assert_array_equal(comp.cpu().numpy(), comp_ref)
+
+
+# ---------------------------------------------------------------- statistics
+@pytest.mark.parametrize("seed,counts,k", [(0, [500], 250), (1, [30, 50, 20], 50), (2, [7, 3, 9, 11], 24),
+                                           (3, [1000, 3], 501)])
+def test_evidence_statistics_match_sequential_update(seed, counts, k):
+    rng = np.random.default_rng(seed)
+    nc = len(counts)
+    pool = np.concatenate([np.full(c, i) for i, c in enumerate(counts)])
+    labels = rng.permutation(pool)[:k].astype(np.int32)
+    logl = np.sort(rng.normal(-50, 20, k))
+    logx0 = np.log(rng.uniform(0.1, 1.0, nc)) - 3.0
+    logzx0 = logx0 - 60.0
+    logxx0 = np.add.outer(logx0, logx0) - 0.01
+    g = ggns.stats_update(counts, logx0, labels, logl, logzx0, logxx0)
+    o = oracle.stats_sequence(counts, logx0, labels, logl, logzx0, logxx0)
+    assert g["logz"] == pytest.approx(o["logz"], rel=1e-12, abs=1e-12)
+    assert g["logz2"] == pytest.approx(o["logz2"], rel=1e-12, abs=1e-12)
+    np.testing.assert_allclose(g["logx"], o["logx"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g["logx2"], o["logx2"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(g["logzx"], o["logzx"], rtol=1e-12, atol=1e-12)
+    # the oracle reports the mass of each kill with the count at that kill; the batch
+    # form gives every kill of cluster c the mass X_c/(n_c+1) of the batch start: equal
+    np.testing.assert_allclose(g["logw"], o["logw"], rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- likelihoods
+@pytest.mark.parametrize("kind,d", [("iso", 2), ("iso", 33), ("mix", 32), ("mix", 7), ("dense", 20),
+                                    ("dense_mix", 24), ("rosen", 9), ("rosen", 2), ("mix", 130)])
+def test_likelihood_and_score_match_oracle(kind, d):
+    w = W.small_workload(kind, d, 20, seed=d)
+    s = ggns.Sampler([w])
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(d)
+    n = 257
+    x = rng.uniform(-0.5, 0.5, (n, d)).astype(np.float32)
+    xd = _dev(x, torch.float32)
+    ll = torch.zeros(n, device="cuda")
+    gr = torch.zeros((n, d), device="cuda")
+    s.lik_forward(xd.data_ptr(), n, ll.data_ptr(), gr.data_ptr())
+    ll, gr = ll.cpu().numpy(), gr.cpu().numpy()
+    for i in range(n):
+        v, g = lik.loglik(x[i].astype(np.float64), grad=True)
+        assert ll[i] == pytest.approx(v, rel=1e-5, abs=1e-4)
+        assert np.linalg.norm(gr[i] - g) <= 1e-4 * max(1.0, np.linalg.norm(g))
+
+
+@pytest.mark.parametrize("kind,d", [("iso", 5), ("mix", 16), ("dense", 12), ("dense_mix", 10)])
+def test_adjoint_matches_oracle(kind, d):
+    w = W.small_workload(kind, d, 20, seed=d + 1)
+    s = ggns.Sampler([w])
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(3)
+    n = 64
+    x = rng.uniform(-0.4, 0.4, (n, d)).astype(np.float32)
+    go = rng.normal(size=n).astype(np.float32)
+    K = lik.n_comp
+    gx = torch.zeros((n, d), device="cuda")
+    gmu = torch.zeros((K, d), device="cuda")
+    xd, god = _dev(x, torch.float32), _dev(go, torch.float32)  # keep both alive across the call
+    s.lik_backward(xd.data_ptr(), n, god.data_ptr(), gx.data_ptr(), gmu.data_ptr())
+    ref_mu = sum(go[i] * lik.dmeans(x[i].astype(np.float64)) for i in range(n))
+    ref_x = np.stack([go[i] * lik.loglik(x[i].astype(np.float64), grad=True)[1] for i in range(n)])
+    assert np.linalg.norm(gmu.cpu().numpy() - ref_mu) <= 1e-4 * max(1.0, np.linalg.norm(ref_mu))
+    assert np.linalg.norm(gx.cpu().numpy() - ref_x) <= 1e-4 * max(1.0, np.linalg.norm(ref_x))
+
+
+# ---------------------------------------------------------------- HSS trajectories
+def _ball_start(d, n, R, rng):
+    v = rng.standard_normal((n, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v * R * rng.uniform(0.2, 0.95, size=(n, 1)) ** (1.0 / d)
+
+
+@pytest.mark.parametrize("kind,d,noise_mode", [("iso", 8, 1), ("iso", 8, 0), ("mix", 32, 1), ("iso", 2, 1),
+                                               ("rosen", 6, 1), ("dense", 16, 1)])
+def test_hss_trajectories_match_oracle(kind, d, noise_mode):
+    """At most 20 steps from identical FP32 inputs: identical inside/outside decisions, step counts
+    and reservoir picks, and outputs within 1e-5 relative.  Inputs whose oracle trajectory comes
+    within 1e-3 (relative) of L* are skipped: there FP32 and FP64 may decide a reflection differently."""
+    w = W.small_workload(kind, d, 40, seed=11)
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(5)
+    n = 16
+    center = np.zeros(d) if kind != "mix" else w["spec"]["means"][0]
+    if kind == "rosen":
+        center = np.full(d, 0.3)
+    found = False
+    for attempt in range(40):
+        x0 = (center + _ball_start(d, n, 0.15, rng)).astype(np.float32).astype(np.float64)
+        l0 = np.array([lik.loglik(v) for v in x0])
+        lstar = float(np.float32(np.min(l0) - 0.5 * abs(np.min(l0)) * 0.02 - 0.5))
+        cfg = oracle.make_cfg(**dict(w["cfg"], n_steps=20, noise_mode=noise_mode,
+                                     delta_p=0.2 if noise_mode else 0.05))
+        o = oracle.hss_batch(lik, w["lo"], w["hi"], cfg, 3, x0, l0, lstar, 0.01, trace=True)
+        ll = o["trace"][:, :, 2 * d]
+        if np.min(np.abs(ll - lstar)) > 1e-3 * max(1.0, abs(lstar)):
+            found = True
+            break
+    assert found
+    s = ggns.Sampler([dict(w, cfg=dict(w["cfg"], n_steps=20, noise_mode=noise_mode,
+                                       delta_p=0.2 if noise_mode else 0.05))])
+    xo = torch.zeros((n, d), device="cuda")
+    lo_ = torch.zeros(n, device="cuda")
+    x0d, l0d = _dev(x0, torch.float32), _dev(l0, torch.float32)  # keep both alive across the call
+    st = s.hss(x0d.data_ptr(), l0d.data_ptr(), n, lstar, 0.01, 3, xo.data_ptr(), lo_.data_ptr())
+    assert st["t_save"] == (o["t_save"] if o["t_save"] > 0 else 21)
+    assert st["t_stop"] == o["t_stop"]
+    assert (st["n_in"], st["n_out"]) == (o["n_in"], o["n_out"])
+    np.testing.assert_allclose(xo.cpu().numpy(), o["x"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(lo_.cpu().numpy(), o["logl"], rtol=1e-5, atol=1e-4)
+
+
+# ---------------------------------------------------------------- full runs
+def _run_gpu(runs):
+    s = ggns.Sampler(runs)
+    s.run()
+    return s, [s.result(r) for r in range(len(runs))]
+
+
+def test_c1_evidence_against_closed_form_and_oracle():
+    w = W.workload("c1")
+    truth = W.truth_logz(w)
+    R = 16
+    runs = [dict(w, cfg=dict(w["cfg"], run_id=r)) for r in range(R)]
+    s, res = _run_gpu(runs)
+    z = np.array([r["logz"] for r in res])
+    e = np.array([r["logz_err"] for r in res])
+    assert all(r["status"] == 0 and r["terminated"] == 1 for r in res)
+    assert np.all(np.abs(z - truth) < 4 * e)
+    assert abs(z.mean() - truth) < 3.5 * e.mean() / math.sqrt(R) + 0.02
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    zo = np.array([oracle.run(lik, w["lo"], w["hi"], oracle.make_cfg(**dict(w["cfg"], run_id=r)))["logz"]
+                   for r in range(R)])
+    se = math.sqrt(z.var() / R + zo.var() / R)
+    assert abs(z.mean() - zo.mean()) < max(0.2, 3 * se)
+
+
+def test_batch_of_uneven_runs_and_posterior():
+    ws = [W.small_workload("iso", 4, 100, seed=1), W.small_workload("mix", 8, 300, seed=2, clustering=1),
+          W.small_workload("rosen", 3, 150, seed=3), W.small_workload("iso", 16, 200, seed=4)]
+    s, res = _run_gpu(ws)
+    for w, r in zip(ws, res):
+        assert r["status"] == 0 and r["terminated"] == 1
+        t = W.truth_logz(w)
+        if t is not None:
+            assert abs(r["logz"] - t) < 5 * r["logz_err"] + 0.3, (w["name"], r["logz"], t)
+    x, lp = s.samples(0)
+    p = np.exp(lp)
+    assert p.sum() == pytest.approx(1.0, abs=1e-6)
+
+
+def test_grad_logz_matches_oracle_on_the_same_dead_points():
+    w = W.small_workload("mix", 4, 200, seed=9)
+    s, res = _run_gpu([w])
+    g = s.grad_logz(0)
+    x, lp = s.samples(0)
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    ref = oracle.grad_logz_means(lik, x, np.zeros(len(lp)), lp, 0.0)
+    assert np.linalg.norm(g - ref) <= 1e-4 * max(1.0, np.linalg.norm(ref))
+
+
+def test_resume_is_bit_identical():
+    w = W.small_workload("mix", 6, 200, seed=12, clustering=1)
+    a = ggns.Sampler([w])
+    a.step(5)
+    blob = a.state_save()
+    a.run()
+    ra = a.result(0)
+    xa, la = a.samples(0)
+    b = ggns.Sampler([w])
+    b.state_load(blob)
+    b.run()
+    rb = b.result(0)
+    xb, lb = b.samples(0)
+    assert ra["logz"] == rb["logz"] and ra["n_iter"] == rb["n_iter"]
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(la, lb)
+
+
+def test_rerun_is_deterministic():
+    w = W.small_workload("mix", 8, 300, seed=13, clustering=1)
+    _, ra = _run_gpu([w])
+    _, rb = _run_gpu([w])
+    assert ra[0]["logz"] == rb[0]["logz"] and ra[0]["n_like"] == rb[0]["n_like"]
