@@ -227,6 +227,23 @@ ns_status ns_hss(const ns_ctx *ctx, const float *x0_dev, const float *logl0_dev,
 ns_status ns_knn_components(const float *x_dev, int m, int d, int *comp_dev, int *n_comp_host,
                             void *stream);
 
+/* Allocation-free form of ns_knn_components, for callers that cannot allocate
+ * device memory when they run it (a host framework that owns all device memory
+ * through its own pool, or a process whose device-memory budget is fixed at
+ * start time).  The paper has no counterpart: this is an interface variant.
+ * Same inputs, outputs and results as ns_knn_components, for m <= 4096 points
+ * and d <= 512; larger m returns NS_ERR_ARG with a message in
+ * ns_last_error(NULL).  Its scratch is one static device array (about 304 KiB)
+ * that every GPU loading the library holds until the process exits; the call
+ * allocates and frees nothing.  The first call on a device, with that device
+ * current, looks up the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array and leaves its contents
+ * behind (each call re-initialises what it reads), so calls that overlap on the
+ * GPU -- on different streams or host threads -- race and must be serialised
+ * by the caller.  Synchronises `stream`. */
+ns_status ns_knn_components_noalloc(const float *x_dev, int m, int d, int *comp_dev, int *n_comp_host,
+                                    void *stream);
+
 /* Order of n log-likelihoods (ascending, NaN first, ties by index):
  * order_dev[n].  n <= 16384. */
 ns_status ns_sort_logl(const float *logl_dev, int n, int *order_dev, void *stream);

@@ -24,7 +24,12 @@
 
 using namespace ggns;
 
+namespace {
+thread_local std::string g_create_error;
+}
+
 namespace ggns {
+void set_global_error(const char *msg) { g_create_error = msg ? msg : ""; }
 const KindLaunch &kind_launch_iso();
 const KindLaunch &kind_launch_mix();
 const KindLaunch &kind_launch_dense();
@@ -46,7 +51,6 @@ namespace {
 
 constexpr int GRAPH_ITERS = 8;
 constexpr size_t SMEM_LIMIT = 200 * 1024;
-thread_local std::string g_create_error;
 
 struct RunClass {
     int kind, tile;

@@ -37,6 +37,9 @@ cudaError_t launch_knn_components(const float *x, int n, int d, const int *label
 cudaError_t launch_stats_plain(Stats *st, double *zz, int k, const double *kL, const int *kP, double *logw,
                                cudaStream_t s);
 
+// message returned by ns_last_error(NULL)
+void set_global_error(const char *msg);
+
 // per likelihood kind (ggns_k_<kind>.cu)
 struct KindLaunch {
     cudaError_t (*prior)(int tile, const DevCtx &C, const int *runs, int nr, int max_n, size_t smem, int pis,

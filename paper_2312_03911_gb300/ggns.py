@@ -52,7 +52,7 @@ EXPORTS = ["ns_config_default", "ns_create", "ns_batch_create", "ns_set_stream",
            "ns_profile", "ns_result",
            "ns_result_run", "ns_samples", "ns_grad_logz", "ns_state_save", "ns_state_load", "ns_last_error",
            "ns_destroy", "ns_philox", "ns_lik_forward", "ns_lik_backward", "ns_hss", "ns_knn_components",
-           "ns_sort_logl", "ns_stats_update"]
+           "ns_sort_logl", "ns_stats_update", "ns_knn_components_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -104,6 +104,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
                              C.POINTER(C.c_long), _vp]
         L.ns_knn_components.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int), _vp]
         L.ns_sort_logl.argtypes = [_vp, C.c_int, _vp, _vp]
+        L.ns_knn_components_noalloc.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int), _vp]
         L.ns_stats_update.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
@@ -277,6 +278,13 @@ def philox(ctr_ptr, key0, key1, out_ptr, n, stream=None):
 def knn_components(x_ptr, m, d, comp_ptr, stream=None) -> int:
     nc = C.c_int()
     _check(load().ns_knn_components(_vp(x_ptr), int(m), int(d), _vp(comp_ptr), C.byref(nc), _vp(stream)))
+    return nc.value
+
+
+def knn_components_noalloc(x_ptr, m, d, comp_ptr, stream=None) -> int:
+    """ns_knn_components_noalloc: the same result without allocating device memory (m <= 4096)."""
+    nc = C.c_int()
+    _check(load().ns_knn_components_noalloc(_vp(x_ptr), int(m), int(d), _vp(comp_ptr), C.byref(nc), _vp(stream)))
     return nc.value
 
 
