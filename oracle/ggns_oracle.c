@@ -456,7 +456,7 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
 /* Ordering: ascending (log L, slot); NaN counts as the lowest                */
 /* ------------------------------------------------------------------------- */
 
-static const double *g_sort_key;
+static _Thread_local const double *g_sort_key; /* per thread: runs may execute concurrently */
 static int orc_cmp_key(const void *a, const void *b)
 {
     int i = *(const int *)a, j = *(const int *)b;
