@@ -271,7 +271,7 @@ def gpu_arm(args):
     zall = np.array(logz)
     out_frac_est = 0.12
     ops = lane_ops_per_point_step(32, 4, out_frac_est)
-    hss_s = prof["hss_ms"] / 1000.0
+    hss_s = prof["hss_ms"] / 1000.0  # time during which HSS kernels of any run were executing
     achieved = ops * (sum(pts)) / hss_s if hss_s > 0 else None
     f_sm = (clocks.get("sm_mhz") or 1447.0) * 1e6
     peak = SMS * FP32_LANES_PER_SM * f_sm
@@ -279,7 +279,8 @@ def gpu_arm(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
             "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
             "kernel": "k_hss (phases 0-2)", "ops_per_point_step": ops,
-            "hss_ms_per_iteration": prof["hss_ms"] / hss_iters,
+            "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
+            "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
             "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}
     # e2e: through the C ABI from host buffers (create = H2D of parameters, result = D2H)
     e2e_t = []
@@ -299,6 +300,20 @@ def gpu_arm(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_pts = pts[-1]
     e2e_value = e2e_pts / (sum(e2e_t) / len(e2e_t))
+    # the plain GPU path: one run per context, one host-synchronised launch chain per iteration
+    plain_ms = None
+    if not args.no_plain:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in runs:
+            sp = ggns.Sampler([r])
+            while not sp.step(1):
+                pass
+            sp.run(0)
+            sp.result(0)
+            sp.close()
+        torch.cuda.synchronize()
+        plain_ms = 1000.0 * (time.perf_counter() - t0)
     line = None
     if rank == 0:
         cpu = None
@@ -313,7 +328,13 @@ def gpu_arm(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
-                "time_to_logz_ms": ms, "logz_mean": float(zall.mean()), "logz_truth": truth,
+                "time_to_logz_ms": ms,
+                "plain": None if plain_ms is None else {
+                    "time_to_logz_ms": plain_ms,
+                    "what": "same replicas one after another, one context each, one host-synchronised launch "
+                            "chain per iteration (no graph, no batching)",
+                    "speedup": plain_ms / ms},
+                "logz_mean": float(zall.mean()), "logz_truth": truth,
                 "dlogz_mean": float(zall.mean() - truth), "logz_err_mean": float(np.mean(errs)),
                 "logz_sd": float(zall.std()),
                 "roofline": roof, "cpu_baseline": cpu,
@@ -338,6 +359,7 @@ def main():
     ap.add_argument("--impl", default="ggns", choices=["ggns", "reference"])
     ap.add_argument("--replicas", type=int, default=DEFAULT_REPLICAS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

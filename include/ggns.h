@@ -137,10 +137,12 @@ ns_status ns_run(ns_ctx *ctx, long max_iters);
  * Used to repeat a workload without allocating.  Synchronises. */
 ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
 
-/* Profiling counters of ctx: out[0] milliseconds spent in the HSS kernels of
- * the iterations ns_run executed (CUDA events around the three HSS phases of
- * each iteration), out[1] those iterations, out[2] kernels launched by ctx,
- * out[3] CUDA-graph replays.  reset != 0 zeroes them after reading. */
+/* Profiling counters of ctx (out[5]): out[0] milliseconds during which at
+ * least one HSS kernel of ns_run was executing (union over the run groups of
+ * the intervals between CUDA events recorded around the three HSS phases of
+ * each iteration), out[1] group-iterations measured, out[2] kernels launched by
+ * ctx, out[3] rounds of graph replays, out[4] the summed (not merged) HSS
+ * intervals.  reset != 0 zeroes them after reading. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 
 typedef struct {

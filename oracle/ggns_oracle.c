@@ -51,7 +51,7 @@ enum {
     ORC_P_INIT = 0,    /* prior draw of live point `slot`                     */
     ORC_P_MOM = 1,     /* initial momentum of walker `slot`                   */
     ORC_P_NOISE = 2,   /* momentum noise eps at step `step`                   */
-    ORC_P_RES = 3,     /* reservoir acceptance word at step `step`            */
+    ORC_P_RES = 3,     /* reserved (the reservoir uses spare bits of the noise) */
     ORC_P_CLUSTER = 4, /* cluster choice of walker `slot`                     */
     ORC_P_START = 5,   /* start-point choice of walker `slot`                 */
     ORC_P_PRUNE = 6    /* fresh momentum after pruning at step `step`         */
@@ -418,9 +418,12 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
         for (int j = 0; j < n; ++j) {
             if (saving && !outside[j]) {
                 ++count[j];
+                /* acceptance word: the low bits of the four words of noise block 0
+                 * of this step, which the uniforms (top 23 bits) leave unused */
                 uint32_t w[4];
-                orc_rng_block(cfg->seed, cfg->run_id, iter, ORC_P_RES, (uint32_t)j, (uint32_t)t, 0, w);
-                if ((((uint64_t)w[0] * (uint64_t)count[j]) >> 32) == 0) {
+                orc_rng_block(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, 0, w);
+                uint32_t word = (w[0] & 511u) | ((w[1] & 511u) << 9) | ((w[2] & 511u) << 18) | ((w[3] & 31u) << 27);
+                if ((((uint64_t)word * (uint64_t)count[j]) >> 32) == 0) {
                     memcpy(xr + (size_t)j * d, x + (size_t)j * d, sizeof(double) * d);
                     lr[j] = logl_now[j];
                 }
@@ -504,7 +507,8 @@ static int orc_cmp_nb(const void *a, const void *b)
 }
 
 /*
- * Algorithm 4 on m points x[m][d] (FP32, the precision the decision is taken in):
+ * Algorithm 4 on m points x[m][d] (FP32, the precision the decision is taken in;
+ * squared distances accumulate in coordinate order, one fmaf per coordinate):
  * for k = 2, 3, ... build the k-nearest-neighbour graph (edge i-j when j is among
  * the k nearest of i, or i among the k nearest of j; Euclidean; ties broken by the
  * lower index; self excluded; k capped at m-1), take its connected components, and
@@ -529,8 +533,7 @@ int orc_knn_components(int m, int d, const float *x, int *comp)
                 float s = 0.0f;
                 for (int t = 0; t < d; ++t) {
                     float diff = x[(size_t)i * d + t] - x[(size_t)j * d + t];
-                    float sq = diff * diff;
-                    s = s + sq;
+                    s = fmaf(diff, diff, s); /* one correctly rounded fused multiply-add per coordinate */
                 }
                 row[c].dist = s; row[c].idx = j; ++c;
             }

@@ -61,6 +61,22 @@ struct RunClass {
     int prec_in_smem = 0;
 };
 
+// Runs advanced together by one CUDA graph on one stream.  Different groups
+// run on different streams, so one run's selection or HSS phases overlap another
+// run's instead of waiting for the slowest walker of the whole batch.
+struct Group {
+    int r0 = 0, nr = 0, max_n = 0;
+    std::vector<RunClass> classes;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[8][2] = {};
+    cudaEvent_t done_ev = nullptr;
+    // the statistics update runs on a second stream, beside the HSS phases
+    cudaStream_t ev_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    int launches_per_iter = 0;
+};
+
 struct DeadHost {
     float *x = nullptr, *logl = nullptr;
     double *logw = nullptr;
@@ -86,9 +102,12 @@ struct ns_ctx {
     unsigned long long *lastkey = nullptr;
     long fa_len = 0, pt_len = 0, w_len = 0;
     std::vector<RunClass> classes;
+    std::vector<Group> groups;
+    cudaEvent_t start_ev = nullptr;
+    double hss_ms_sum = 0.0;
     bool any_clustering = false;
     int max_n = 0, max_d = 0;
-    size_t sel_smem = 0, knn_smem = 0, cl_smem = 0;
+    size_t sel_smem = 0, knn_smem = 0, cl_smem = 0, sort_smem = 0;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -318,28 +337,36 @@ ns_status ensure_dead_capacity(ns_ctx *ctx, int iters, const std::vector<RunStat
     return NS_OK;
 }
 
-ns_status launch_iteration(ns_ctx *ctx, cudaStream_t s, int ev_slot)
+ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
 {
     const DevCtx &C = ctx->dc;
     int n = 0;
     if (ctx->any_clustering) {
-        CU(launch_knn(C, ctx->n_runs, ctx->max_n, ctx->knn_smem, s));
-        CU(launch_cluster(C, ctx->n_runs, ctx->lastkey, ctx->cl_smem, s));
+        CU(launch_knn(C, g.r0, g.nr, g.max_n, ctx->knn_smem, s));
+        CU(launch_cluster(C, g.r0, g.nr, ctx->lastkey, ctx->cl_smem, s));
         n += 2;
     }
-    CU(launch_select(C, ctx->n_runs, ctx->sel_smem, s));
+    CU(launch_sort(C, g.r0, g.nr, ctx->sort_smem, s));
     ++n;
-    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(ctx->ev[ev_slot][0], s, cudaEventRecordExternal));
+    // fork: the FP64 statistics of this iteration's kills beside the HSS phases
+    CU(cudaEventRecord(g.fork_ev, s));
+    CU(cudaStreamWaitEvent(g.ev_stream, g.fork_ev, 0));
+    CU(launch_evidence(C, g.r0, g.nr, ctx->sel_smem, g.ev_stream));
+    CU(cudaEventRecord(g.join_ev, g.ev_stream));
+    ++n;
+    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][0], s, cudaEventRecordExternal));
     for (int phase = 0; phase < 3; ++phase)
-        for (auto &cl : ctx->classes) {
+        for (auto &cl : g.classes) {
             CU(kind_launch(cl.kind).hss(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, phase, cl.smem,
                                         cl.prec_in_smem, s));
             ++n;
         }
-    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(ctx->ev[ev_slot][1], s, cudaEventRecordExternal));
-    CU(launch_tail(C, ctx->n_runs, s));
+    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][1], s, cudaEventRecordExternal));
+    // join before the tail: termination reads the statistics
+    CU(cudaStreamWaitEvent(s, g.join_ev, 0));
+    CU(launch_tail(C, g.r0, g.nr, s));
     ++n;
-    ctx->launches_per_iter = n;
+    g.launches_per_iter = n;
     return NS_OK;
 }
 
@@ -406,7 +433,7 @@ ns_status read_states(ns_ctx *ctx, std::vector<RunState> &st)
 
 ns_status finish_runs(ns_ctx *ctx)
 {
-    CU(launch_final(ctx->dc, ctx->n_runs, ctx->sel_smem, ctx->stream));
+    CU(launch_final(ctx->dc, 0, ctx->n_runs, ctx->sel_smem, ctx->stream));
     ++ctx->launches;
     CU(cudaStreamSynchronize(ctx->stream));
     return NS_OK;
@@ -554,12 +581,6 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
     ctx->cfg.assign(cfg, cfg + n_runs);
     CK(setup());
     CK(init_state(ctx));
-    auto mkev = [&]() -> ns_status {
-        for (int i = 0; i < GRAPH_ITERS; ++i)
-            for (int j = 0; j < 2; ++j) CU(cudaEventCreate(&ctx->ev[i][j]));
-        return NS_OK;
-    };
-    CK(mkev());
     DevCtx &C = ctx->dc;
     C.n_runs = n_runs;
     C.desc = ctx->desc_dev;
@@ -619,11 +640,58 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         };
         CK(setup_cls());
     }
+    // run groups: one stream and one graph each (GGNS_RUNS_PER_GROUP runs; default: all runs in one group)
+    {
+        int per = n_runs;
+        if (const char *v = getenv("GGNS_RUNS_PER_GROUP")) per = std::max(1, atoi(v));
+        per = std::max(per, (n_runs + 127) / 128);
+        auto mkgroups = [&]() -> ns_status {
+            CU(cudaEventCreateWithFlags(&ctx->start_ev, cudaEventDefault));
+            for (int r0 = 0; r0 < n_runs; r0 += per) {
+                Group g;
+                g.r0 = r0;
+                g.nr = std::min(per, n_runs - r0);
+                std::map<std::pair<int, int>, int> gcls;
+                for (int r = g.r0; r < g.r0 + g.nr; ++r) {
+                    const RunDesc &D = ctx->desc[r];
+                    g.max_n = std::max(g.max_n, D.n_live);
+                    auto key = std::make_pair(D.kind, D.tile);
+                    if (!gcls.count(key)) {
+                        gcls[key] = (int)g.classes.size();
+                        RunClass rc = ctx->classes[cls[key]];
+                        rc.runs.clear();
+                        rc.runs_dev = nullptr;
+                        rc.max_k = rc.max_n = 0;
+                        g.classes.push_back(rc);
+                    }
+                    RunClass &rc = g.classes[gcls[key]];
+                    rc.runs.push_back(r);
+                    rc.max_k = std::max(rc.max_k, D.k);
+                    rc.max_n = std::max(rc.max_n, D.n_live);
+                }
+                for (auto &rc : g.classes) {
+                    CU(cudaMalloc(&rc.runs_dev, sizeof(int) * rc.runs.size()));
+                    CU(cudaMemcpy(rc.runs_dev, rc.runs.data(), sizeof(int) * rc.runs.size(), cudaMemcpyHostToDevice));
+                }
+                CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+                CU(cudaStreamCreateWithFlags(&g.ev_stream, cudaStreamNonBlocking));
+                CU(cudaEventCreateWithFlags(&g.fork_ev, cudaEventDisableTiming));
+                CU(cudaEventCreateWithFlags(&g.join_ev, cudaEventDisableTiming));
+                for (int i = 0; i < GRAPH_ITERS; ++i)
+                    for (int j = 0; j < 2; ++j) CU(cudaEventCreate(&g.ev[i][j]));
+                CU(cudaEventCreateWithFlags(&g.done_ev, cudaEventDisableTiming));
+                ctx->groups.push_back(g);
+            }
+            return NS_OK;
+        };
+        CK(mkgroups());
+    }
     ctx->sel_smem = select_smem_bytes(ctx->max_n);
     ctx->knn_smem = knn_smem_bytes(ctx->max_d);
     ctx->cl_smem = cluster_smem_bytes(ctx->max_n);
+    ctx->sort_smem = sort_smem_bytes(ctx->max_n);
     auto attrs = [&]() -> ns_status {
-        CU(prepare_iteration_kernels(ctx->sel_smem, ctx->knn_smem, ctx->cl_smem));
+        CU(prepare_iteration_kernels(ctx->sel_smem, ctx->knn_smem, ctx->cl_smem, ctx->sort_smem));
         return NS_OK;
     };
     CK(attrs());
@@ -660,11 +728,12 @@ ns_status ns_step(ns_ctx *ctx, int n_iters, int *done)
     if (s != NS_OK) return s;
     s = ensure_dead_capacity(ctx, n_iters, st);
     if (s != NS_OK) return s;
-    for (int i = 0; i < n_iters; ++i) {
-        s = launch_iteration(ctx, ctx->stream, -1);
-        if (s != NS_OK) return s;
-        ctx->launches += ctx->launches_per_iter;
-    }
+    for (int i = 0; i < n_iters; ++i)
+        for (auto &g : ctx->groups) {
+            s = launch_iteration(ctx, g, ctx->stream, -1);
+            if (s != NS_OK) return s;
+            ctx->launches += g.launches_per_iter;
+        }
     s = read_states(ctx, st);
     if (s != NS_OK) return s;
     int all = 1;
@@ -679,22 +748,24 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
     std::vector<RunState> st;
     ns_status s = read_states(ctx, st);
     if (s != NS_OK) return s;
-    if (!ctx->graph) {
-        // capture GRAPH_ITERS iterations once; kernels of finished runs return at once
-        cudaGraph_t g;
-        CU(cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal));
+    for (auto &g : ctx->groups) {
+        if (g.graph) continue;
+        // capture GRAPH_ITERS iterations of this group once; kernels of finished runs return at once
+        cudaGraph_t gr;
+        CU(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
         for (int i = 0; i < GRAPH_ITERS; ++i) {
-            s = launch_iteration(ctx, ctx->graph_stream, i);
+            s = launch_iteration(ctx, g, g.stream, i);
             if (s != NS_OK) {
-                cudaStreamEndCapture(ctx->graph_stream, &g);
+                cudaStreamEndCapture(g.stream, &gr);
                 return s;
             }
         }
-        CU(cudaStreamEndCapture(ctx->graph_stream, &g));
-        CU(cudaGraphInstantiate(&ctx->graph, g, 0));
-        cudaGraphDestroy(g);
+        CU(cudaStreamEndCapture(g.stream, &gr));
+        CU(cudaGraphInstantiate(&g.graph, gr, 0));
+        cudaGraphDestroy(gr);
     }
     long done_iters = 0;
+    std::vector<std::pair<float, float>> spans;
     for (;;) {
         int all = 1;
         for (auto &x : st) all &= x.done;
@@ -703,18 +774,52 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
         if (s != NS_OK) return s;
         std::vector<int> it0(ctx->n_runs);
         for (int r = 0; r < ctx->n_runs; ++r) it0[r] = st[r].iter;
-        CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+        CU(cudaEventRecord(ctx->start_ev, ctx->stream));
+        std::vector<int> launched(ctx->groups.size(), 0);
+        for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+            Group &g = ctx->groups[gi];
+            bool busy = false;
+            for (int r = g.r0; r < g.r0 + g.nr; ++r) busy |= !st[r].done;
+            if (!busy) continue;
+            launched[gi] = 1;
+            CU(cudaStreamWaitEvent(g.stream, ctx->start_ev, 0));
+            CU(cudaGraphLaunch(g.graph, g.stream));
+            CU(cudaEventRecord(g.done_ev, g.stream));
+            CU(cudaStreamWaitEvent(ctx->stream, g.done_ev, 0));
+            ctx->launches += (long)GRAPH_ITERS * g.launches_per_iter;
+        }
         done_iters += GRAPH_ITERS;
         s = read_states(ctx, st);
         if (s != NS_OK) return s;
-        int active = 0;
-        for (int r = 0; r < ctx->n_runs; ++r) active = std::max(active, st[r].iter - it0[r]);
-        for (int i = 0; i < active && i < GRAPH_ITERS; ++i) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess) ctx->hss_ms += ms;
+        // HSS activity: union over groups of the intervals between the events around the three phases
+        spans.clear();
+        for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+            if (!launched[gi]) continue;
+            Group &g = ctx->groups[gi];
+            int active = 0;
+            for (int r = g.r0; r < g.r0 + g.nr; ++r) active = std::max(active, st[r].iter - it0[r]);
+            for (int i = 0; i < active && i < GRAPH_ITERS; ++i) {
+                float a = 0.f, b = 0.f;
+                if (cudaEventElapsedTime(&a, ctx->start_ev, g.ev[i][0]) == cudaSuccess &&
+                    cudaEventElapsedTime(&b, ctx->start_ev, g.ev[i][1]) == cudaSuccess && b >= a) {
+                    spans.push_back({a, b});
+                    ctx->hss_ms_sum += b - a;
+                }
+            }
+            ctx->hss_iters += active;
         }
-        ctx->hss_iters += active;
-        ctx->launches += (long)GRAPH_ITERS * ctx->launches_per_iter;
+        std::sort(spans.begin(), spans.end());
+        float cur_a = -1.f, cur_b = -1.f;
+        for (auto &sp : spans) {
+            if (sp.first > cur_b) {
+                if (cur_b > cur_a) ctx->hss_ms += cur_b - cur_a;
+                cur_a = sp.first;
+                cur_b = sp.second;
+            } else {
+                cur_b = std::max(cur_b, sp.second);
+            }
+        }
+        if (cur_b > cur_a) ctx->hss_ms += cur_b - cur_a;
         ++ctx->replays;
     }
     int all = 1;
@@ -753,8 +858,9 @@ ns_status ns_profile(const ns_ctx *cctx, double *out, int reset)
     out[1] = (double)ctx->hss_iters;
     out[2] = (double)ctx->launches;
     out[3] = (double)ctx->replays;
+    out[4] = ctx->hss_ms_sum;
     if (reset) {
-        ctx->hss_ms = 0.0;
+        ctx->hss_ms = ctx->hss_ms_sum = 0.0;
         ctx->hss_iters = ctx->launches = ctx->replays = 0;
     }
     return NS_OK;
@@ -781,11 +887,11 @@ ns_status ns_result_run(const ns_ctx *cctx, int run, ns_result_t *out)
     out->terminated = S.terminated;
     out->status = S.status;
     if (S.final_done && S.n_dead > 0 && std::isfinite(S.logz)) {
-        ns_status es = ensure_scratch(ctx, 2);
+        ns_status es = ensure_scratch(ctx, 2 + 2 * 152);
         if (es != NS_OK) return es;
         double *tmp = ctx->scratch;
         CU(launch_info(ctx->dc, run, S.logz, tmp, ctx->stream));
-        ++ctx->launches;
+        ctx->launches += 2;
         double h[2];
         CU(cudaMemcpyAsync(h, tmp, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
@@ -960,6 +1066,20 @@ void ns_destroy(ns_ctx *ctx)
 {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (auto &g : ctx->groups) {
+        if (g.graph) cudaGraphExecDestroy(g.graph);
+        for (auto &rc : g.classes)
+            if (rc.runs_dev) cudaFree(rc.runs_dev);
+        for (int i = 0; i < GRAPH_ITERS; ++i)
+            for (int j = 0; j < 2; ++j)
+                if (g.ev[i][j]) cudaEventDestroy(g.ev[i][j]);
+        if (g.done_ev) cudaEventDestroy(g.done_ev);
+        if (g.fork_ev) cudaEventDestroy(g.fork_ev);
+        if (g.join_ev) cudaEventDestroy(g.join_ev);
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.ev_stream) cudaStreamDestroy(g.ev_stream);
+    }
+    if (ctx->start_ev) cudaEventDestroy(ctx->start_ev);
     for (auto &rc : ctx->classes)
         if (rc.runs_dev) cudaFree(rc.runs_dev);
     for (auto &d : ctx->dead) {

@@ -86,6 +86,10 @@ struct RunState {
     int final_done;
     int n_fallback;
     double logz, logz2;
+    long dead_base;        // first dead row of the current iteration's kills
+    int ev_pending;        // the iteration's statistics update has not run yet
+    int kill_cnt[CMAX];    // kills per cluster in the current iteration
+    int spawn_cnt[CMAX];   // new points per cluster in the current iteration
 };
 
 // FP64 cluster statistics of one run (Appendix H), log space.
@@ -170,20 +174,30 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &z0, fl
     z1 = rad * s;
 }
 
+// 32 bits from the low 9 bits of the four words of a block: the bits the
+// uniforms below do not use (they take the top 23 bits of each word).
+__device__ __forceinline__ uint32_t spare_bits(const U4 &w)
+{
+    return (w.x & 511u) | ((w.y & 511u) << 9) | ((w.z & 511u) << 18) | ((w.w & 31u) << 27);
+}
+
 // The E normals of components c0 .. c0+E-1 (c0 a multiple of E; E in {1,2,4,8,16}).
+// *spare (may be null) receives spare_bits of the lane's first block.
 template <int E>
 __device__ __forceinline__ void lane_normals(const RunDesc &D, uint32_t iter, uint32_t purpose, uint32_t slot,
-                                             uint32_t step, int c0, float (&z)[E])
+                                             uint32_t step, int c0, float (&z)[E], uint32_t *spare = nullptr)
 {
     if constexpr (E >= 4) {
 #pragma unroll
         for (int b = 0; b < E / 4; ++b) {
             const U4 w = rng_block(D, iter, purpose, slot, step, static_cast<uint32_t>((c0 >> 2) + b));
+            if (b == 0 && spare) *spare = spare_bits(w);
             box_muller(w.x, w.y, z[4 * b + 0], z[4 * b + 1]);
             box_muller(w.z, w.w, z[4 * b + 2], z[4 * b + 3]);
         }
     } else {
         const U4 w = rng_block(D, iter, purpose, slot, step, static_cast<uint32_t>(c0 >> 2));
+        if (spare) *spare = spare_bits(w);
         const int off = c0 & 3;
         float a0, a1;
         if (off < 2) box_muller(w.x, w.y, a0, a1);

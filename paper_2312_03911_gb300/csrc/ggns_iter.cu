@@ -70,7 +70,7 @@ constexpr int EV_THREADS = 256;
 constexpr int EV_CB = 8;  // target clusters per pass
 
 struct EvScratch {
-    double buf[EV_CB][EV_THREADS];
+    double wtot[EV_CB][EV_THREADS / 32];
     double coef[EV_CB][CMAX];
     double S1[CMAX], S2[CMAX], U[CMAX], V[CMAX];
     int m[CMAX];
@@ -158,42 +158,55 @@ __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, co
                 }
             }
         }
-        // exclusive scans over threads of R and S1 (sequential per target: deterministic)
+        // exclusive scans over threads of R and S1: warp shuffle scans, then the
+        // eight warp totals in order (a fixed order: deterministic)
+        const int lane = tid & 31, warp = tid >> 5;
         for (int pass = 0; pass < 2; ++pass) {
-            if (tid < EV_THREADS) {
+            double v[EV_CB], x[EV_CB];
 #pragma unroll
-                for (int b = 0; b < EV_CB; ++b) E->buf[b][tid] = pass == 0 ? R[b] : S1l[b];
-            }
-            __syncthreads();
-            if (tid < nb) {
-                double run = 0.0;
-                for (int t2 = 0; t2 < EV_THREADS; ++t2) {
-                    const double v = E->buf[tid][t2];
-                    E->buf[tid][t2] = run;
-                    run += v;
+            for (int bb = 0; bb < EV_CB; ++bb) x[bb] = v[bb] = (pass == 0) ? R[bb] : S1l[bb];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int bb = 0; bb < EV_CB; ++bb) {
+                    const double y = __shfl_up_sync(0xffffffffu, x[bb], o);
+                    if (lane >= o) x[bb] += y;
                 }
             }
-            __syncthreads();
-            if (tid < EV_THREADS) {
+            if (lane == 31) {
 #pragma unroll
-                for (int b = 0; b < EV_CB; ++b) {
-                    if (pass == 0) Vl[b] += S1l[b] * E->buf[b][tid];
-                    else Ul[b] += S1l[b] * E->buf[b][tid];
-                }
+                for (int bb = 0; bb < EV_CB; ++bb) E->wtot[bb][warp] = x[bb];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int bb = 0; bb < EV_CB; ++bb) {
+                double off = 0.0;
+                for (int w2 = 0; w2 < warp; ++w2) off += E->wtot[bb][w2];
+                const double excl = off + x[bb] - v[bb];
+                if (pass == 0) Vl[bb] += S1l[bb] * excl;
+                else Ul[bb] += S1l[bb] * excl;
             }
             __syncthreads();
         }
-        // reductions over threads (sequential per target)
+        // reductions over threads: warp trees, then the warp partials in order
         for (int qty = 0; qty < 4; ++qty) {
-            if (tid < EV_THREADS) {
+            double x[EV_CB];
 #pragma unroll
-                for (int b = 0; b < EV_CB; ++b)
-                    E->buf[b][tid] = qty == 0 ? S1l[b] : (qty == 1 ? S2l[b] : (qty == 2 ? Ul[b] : Vl[b]));
+            for (int bb = 0; bb < EV_CB; ++bb)
+                x[bb] = qty == 0 ? S1l[bb] : (qty == 1 ? S2l[bb] : (qty == 2 ? Ul[bb] : Vl[bb]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int bb = 0; bb < EV_CB; ++bb) x[bb] += __shfl_xor_sync(0xffffffffu, x[bb], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int bb = 0; bb < EV_CB; ++bb) E->wtot[bb][warp] = x[bb];
             }
             __syncthreads();
             if (tid < nb) {
                 double sacc = 0.0;
-                for (int t2 = 0; t2 < EV_THREADS; ++t2) sacc += E->buf[tid][t2];
+                for (int w2 = 0; w2 < EV_THREADS / 32; ++w2) sacc += E->wtot[tid][w2];
                 const int c = E->alive_list[pb + tid];
                 if (qty == 0) E->S1[c] = sacc;
                 else if (qty == 1) E->S2[c] = sacc;
@@ -302,18 +315,24 @@ __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, co
 // Selection, statistics and spawn of one iteration (Algorithm 3), one CTA per run.
 // dynamic smem: npow2 keys (8 B) | EvScratch
 // ------------------------------------------------------------------------
-constexpr int SEL_THREADS = 1024;
+constexpr int SEL_THREADS = 256;
 
 __device__ void select_body(DevCtx C, int r, bool final_sweep)
 {
     extern __shared__ unsigned char sraw[];
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
-    Stats *st = C.stats + r;
     const int n = D.n_live;
     const int npow = next_pow2(n);
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(sraw);
     EvScratch *E = reinterpret_cast<EvScratch *>(sraw + key_region_bytes(n));
+    // the run's statistics live in shared memory for the whole kernel
+    Stats *st = reinterpret_cast<Stats *>(sraw + key_region_bytes(n) + ((sizeof(EvScratch) + 15) & ~size_t(15)));
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(C.stats + r);
+        int4 *dst = reinterpret_cast<int4 *>(st);
+        for (int i = threadIdx.x; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
+    }
     __shared__ int s_abort;
     __shared__ double s_lx[2];
     __shared__ int s_cnt[CMAX];
@@ -354,6 +373,12 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
     __syncthreads();
     const long dbase = D.dead_off + S->n_dead;
     evidence_batch(st, &S->logz, &S->logz2, k, kL, kP, E);
+    auto store_stats = [&]() {
+        __syncthreads();
+        const int4 *src = reinterpret_cast<const int4 *>(st);
+        int4 *dst = reinterpret_cast<int4 *>(C.stats + r);
+        for (int i = threadIdx.x; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
+    };
     // dead records: log L, log prior mass, label (x rows are archived by the walkers)
     for (int j = tid; j < k; j += blockDim.x) {
         D.dead_logl[dbase + j] = (float)kL[j];
@@ -374,6 +399,7 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
             S->final_done = 1;
             if (!(S->logz == S->logz)) S->status = NS_ERR_NUMERIC;
         }
+        store_stats();
         return;
     }
     if (tid == 0) {
@@ -411,7 +437,10 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
         }
     }
     __syncthreads();
-    if (S->done) return;
+    if (S->done) {
+        store_stats();
+        return;
+    }
     // ---- survivors sorted by (label, slot)
     for (int i = tid; i < npow; i += blockDim.x) keys[i] = ~0ull;
     __syncthreads();
@@ -457,6 +486,7 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
     }
     __syncthreads();
     if (tid < CMAX && st->alive[tid]) st->n[tid] += s_cnt[tid];
+    store_stats();
     if (tid == 0) {
         S->wcount[0] = S->wcount[1] = S->wcount[2] = 0;
         S->t_save = 0;
@@ -467,28 +497,263 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
     }
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_select(DevCtx C)
+// ------------------------------------------------------------------------
+// Selection and spawn of one iteration (Algorithm 3), one CTA of SORT_THREADS
+// per run.  Only the prior volumes enter the spawn, and their batch update is a
+// closed form (X_c (n_c - m_c + 1)/(n_c + 1)), so the FP64 moment update of
+// Appendix H (k_evidence) runs beside the HSS phases instead of before them.
+// dynamic smem: key region (npow2 x 8 bytes, reused for the survivor lists).
+// ------------------------------------------------------------------------
+constexpr int SORT_THREADS = 1024;
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
 {
-    const int r = blockIdx.x;
-    if (C.state[r].done) return;
-    select_body(C, r, false);
+    extern __shared__ unsigned char sraw[];
+    const int r = r0 + blockIdx.x;
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done) return;
+    const Stats *st = C.stats + r;
+    const int n = D.n_live, k = D.k;
+    const int npow = next_pow2(n);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(sraw);
+    __shared__ int s_abort, s_na, s_alive_list[CMAX];
+    __shared__ int s_m[CMAX], s_cnt[CMAX], s_start[CMAX], s_surv[CMAX];
+    __shared__ double s_w[CMAX], s_cum[CMAX], s_total;
+    __shared__ int s_wsum[SORT_THREADS / 32];
+    const float *logl = C.logl + D.pt_off;
+    const int *label = C.label + D.pt_off;
+    int *ordr = C.order + D.pt_off;
+
+    // ---- ascending (log L, slot) order; NaN first
+    for (int i = tid; i < npow; i += blockDim.x)
+        keys[i] = (i < n) ? ((unsigned long long)float_key(logl[i]) << 32) | (unsigned)i : ~0ull;
+    if (tid < CMAX) {
+        s_m[tid] = 0;
+        s_cnt[tid] = 0;
+    }
+    __syncthreads();
+    block_bitonic_sort(keys, npow);
+    for (int i = tid; i < n; i += blockDim.x) ordr[i] = (int)(keys[i] & 0xffffffffu);
+    if (tid == 0) {
+        s_abort = 0;
+        if (S->n_dead + k > D.dead_cap) {
+            S->status = NS_ERR_CAPACITY;
+            S->done = 1;
+            S->final_done = 1;
+            s_abort = 1;
+        }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    // ---- dead records of the kills (log L, label); x rows are archived by the walkers
+    const long dbase = S->n_dead;
+    for (int j = tid; j < k; j += blockDim.x) {
+        const int s0 = (int)(keys[j] & 0xffffffffu);
+        const int c = label[s0];
+        D.dead_logl[dbase + j] = logl[s0];
+        D.dead_label[dbase + j] = c;
+        atomicAdd(&s_m[c], 1);
+    }
+    __syncthreads();
+    // ---- prior volumes after the kills, in closed form; spawn weights Xbar_c / max Xbar
+    if (tid < CMAX) {
+        const int c = tid;
+        const int left = st->alive[c] ? st->n[c] - s_m[c] : 0;
+        s_surv[c] = left > 0 ? left : 0;
+        s_w[c] = (left > 0) ? st->logXp[c] + log((double)left + 1.0) - log((double)st->n[c] + 1.0) : -INFINITY;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double mx = -INFINITY;
+        int na = 0, off = 0;
+        for (int c = 0; c < CMAX; ++c) {
+            s_start[c] = off;
+            if (s_surv[c] > 0) {
+                mx = fmax(mx, s_w[c]);
+                s_alive_list[na++] = c;
+                off += s_surv[c];
+            }
+        }
+        s_na = na;
+        s_total = mx;
+    }
+    __syncthreads();
+    if (tid < CMAX) s_w[tid] = (s_surv[tid] > 0) ? exp(s_w[tid] - s_total) : 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        // cumulative weights in cluster-id order (FP64)
+        double cum = 0.0;
+        for (int a = 0; a < s_na; ++a) {
+            const int c = s_alive_list[a];
+            cum += s_w[c];
+            s_cum[c] = cum;
+        }
+        s_total = cum;
+        if (s_na == 0) {
+            S->status = NS_ERR_NUMERIC;
+            S->done = 1;
+        }
+    }
+    __syncthreads();
+    if (S->done) return;
+    // ---- survivors of each cluster in slot order: ordered compaction, one cluster at a time
+    unsigned char *killed = reinterpret_cast<unsigned char *>(keys);  // keys are no longer needed
+    int *surv = reinterpret_cast<int *>(sraw + ((npow + 15) & ~15));
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) killed[i] = 0;
+    __syncthreads();
+    for (int j = tid; j < k; j += blockDim.x) killed[ordr[j]] = 1;
+    __syncthreads();
+    const int na = s_na;
+    for (int a = 0; a < na; ++a) {
+        const int c = s_alive_list[a];
+        int base = s_start[c];
+        for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+            const int i = i0 + tid;
+            const int f = (i < n && !killed[i] && label[i] == c) ? 1 : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) s_wsum[warp] = __popc(bal);
+            __syncthreads();
+            int off = base;
+            for (int w2 = 0; w2 < warp; ++w2) off += s_wsum[w2];
+            if (f) {
+                const int pos = off + __popc(bal & ((1u << lane) - 1u));
+                if (pos < n) surv[pos] = i;
+            }
+            int tot = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += s_wsum[w2];
+            __syncthreads();
+            base += tot;
+        }
+        if (tid == 0 && base - s_start[c] != s_surv[c]) s_abort = 1;  // counts and labels disagree
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            S->status = NS_ERR_NUMERIC;
+            S->done = 1;
+        }
+        return;
+    }
+    // ---- spawn: cluster with probability Xbar_c / sum Xbar, then a uniform surviving member
+    const uint32_t iter = (uint32_t)S->iter;
+    for (int j = tid; j < k; j += blockDim.x) {
+        const U4 w = rng_block(D, iter, P_CLUSTER, j, 0, 0);
+        const double target = u01_52(w.x, w.y) * s_total;
+        int chosen = s_alive_list[na - 1];
+        for (int a = 0; a < na; ++a) {
+            const int c = s_alive_list[a];
+            if (target < s_cum[c]) {
+                chosen = c;
+                break;
+            }
+        }
+        const int m = s_surv[chosen];
+        const U4 w2 = rng_block(D, iter, P_START, j, 0, 0);
+        const int pick = (int)(((unsigned long long)w2.x * (unsigned long long)m) >> 32);
+        C.start_slot[D.w_off + j] = surv[s_start[chosen] + pick];
+        C.new_label[D.w_off + j] = chosen;
+        atomicAdd(&s_cnt[chosen], 1);
+    }
+    __syncthreads();
+    if (tid < CMAX) {
+        S->kill_cnt[tid] = s_m[tid];
+        S->spawn_cnt[tid] = s_cnt[tid];
+    }
+    if (tid == 0) {
+        S->lstar = (double)logl[ordr[k - 1]];
+        S->dead_base = dbase;
+        S->n_dead = dbase + k;
+        S->ev_pending = 1;
+        S->wcount[0] = S->wcount[1] = S->wcount[2] = 0;
+        S->t_save = 0;
+        S->t_stop = 0;
+        S->n_in = 0;
+        S->n_out = 0;
+    }
 }
 
-__global__ void __launch_bounds__(SEL_THREADS) k_final(DevCtx C)
+// ------------------------------------------------------------------------
+// Appendix H statistics of the iteration's kills (FP64), beside the HSS phases.
+// Reads the kills from the dead records, writes their log prior masses, applies
+// the spawn counts and the XL statistic.  dynamic smem: kill arrays | EvScratch | Stats
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(SEL_THREADS) k_evidence(DevCtx C, int r0)
 {
-    const int r = blockIdx.x;
+    extern __shared__ unsigned char sraw[];
+    const int r = r0 + blockIdx.x;
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (!S->ev_pending) return;
+    const int k = D.k;
+    double *kL = reinterpret_cast<double *>(sraw);
+    int *kP = reinterpret_cast<int *>(kL + k);
+    EvScratch *E = reinterpret_cast<EvScratch *>(sraw + key_region_bytes(D.n_live));
+    Stats *st = reinterpret_cast<Stats *>(sraw + key_region_bytes(D.n_live) + ((sizeof(EvScratch) + 15) & ~size_t(15)));
+    const int tid = threadIdx.x;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(C.stats + r);
+        int4 *dst = reinterpret_cast<int4 *>(st);
+        for (int i = tid; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    const long dbase = S->dead_base;
+    for (int j = tid; j < k; j += blockDim.x) {
+        kL[j] = (double)D.dead_logl[dbase + j];
+        kP[j] = D.dead_label[dbase + j];
+    }
+    __syncthreads();
+    evidence_batch(st, &S->logz, &S->logz2, k, kL, kP, E);
+    for (int j = tid; j < k; j += blockDim.x) D.dead_logw[dbase + j] = E->logw[kP[j]];
+    __syncthreads();
+    if (tid < CMAX && st->alive[tid]) st->n[tid] += S->spawn_cnt[tid];
+    __syncthreads();
+    if (tid == 0) {
+        // XL statistic on the dead-point sequence: log X (after the kills) + L*
+        double lx = -INFINITY;
+        int na = 0;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c]) {
+                lx = log_add(lx, st->logXp[c]);
+                ++na;
+            }
+        S->log_xl = lx + S->lstar;
+        S->n_clusters = na;
+        S->ev_pending = 0;
+    }
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(st);
+        int4 *dst = reinterpret_cast<int4 *>(C.stats + r);
+        for (int i = tid; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) k_final(DevCtx C, int r0)
+{
+    const int r = r0 + blockIdx.x;
     if (!C.state[r].done || C.state[r].final_done) return;
     select_body(C, r, true);
 }
 
-size_t select_smem_bytes(int n_live_max) { return key_region_bytes(n_live_max) + sizeof(EvScratch); }
+size_t sort_smem_bytes(int n_live_max)
+{
+    const size_t np = (size_t)next_pow2(n_live_max);
+    const size_t a = np * 8, b = ((np + 15) & ~size_t(15)) + 4 * (size_t)n_live_max;
+    return a > b ? a : b;
+}
+
+size_t select_smem_bytes(int n_live_max)
+{
+    return key_region_bytes(n_live_max) + ((sizeof(EvScratch) + 15) & ~size_t(15)) + sizeof(Stats);
+}
 
 // ------------------------------------------------------------------------
 // Iteration tail: step-size rule (Algorithm 3), counters, termination test.
 // ------------------------------------------------------------------------
-__global__ void k_tail(DevCtx C)
+__global__ void k_tail(DevCtx C, int r0)
 {
-    const int r = blockIdx.x;
+    const int r = r0 + blockIdx.x;
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done) return;
@@ -538,22 +803,45 @@ __global__ void k_tail(DevCtx C)
 // k-NN ranks 1..KNN_K of point i among the points with the same label, by
 // ascending (FP32 squared distance, index); the distance is accumulated in
 // coordinate order with round-to-nearest and no contraction.
-constexpr int KNN_WARPS = 8;
-constexpr int KNN_TILE = 32;
+constexpr int KNN_WARPS = 16;
 
+__host__ __device__ __forceinline__ int knn_tile_rows(int d) { return d < 64 ? 128 : (d < 128 ? 64 : 32); }
+
+// Squared distance in coordinate order: each squared difference is added with
+// a correctly rounded fused multiply-add (the oracle uses C's fmaf).
 __device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d)
 {
     float s = 0.f;
     for (int t = 0; t < d; ++t) {
         const float df = __fsub_rn(a[t], b[t]);
-        s = __fadd_rn(s, __fmul_rn(df, df));
+        s = __fmaf_rn(df, df, s);
     }
     return s;
 }
 
-__device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
-                         float *tile /* [KNN_TILE][d+1] */, float *xi_s /* [KNN_WARPS][d] */)
+__device__ __forceinline__ void knn_insert(unsigned long long (&L)[KNN_K], unsigned long long key)
 {
+    if (key < L[KNN_K - 1]) {
+        L[KNN_K - 1] = key;
+#pragma unroll
+        for (int q = KNN_K - 1; q > 0; --q) {
+            if (L[q] < L[q - 1]) {
+                const unsigned long long tmp = L[q];
+                L[q] = L[q - 1];
+                L[q - 1] = tmp;
+            }
+        }
+    }
+}
+
+// One warp per query point; the candidates stream through shared memory in
+// tiles of knn_tile_rows(d) rows, each lane scoring TR/32 of them per tile with
+// independent accumulation chains.
+template <int PER_LANE>
+__device__ void knn_rows_t(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+                           float *tile, float *xi_s, int *tlab)
+{
+    constexpr int TR = 32 * PER_LANE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * KNN_WARPS + warp;
     const bool act = i < n;
@@ -565,27 +853,32 @@ __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *l
     unsigned long long L[KNN_K];
 #pragma unroll
     for (int q = 0; q < KNN_K; ++q) L[q] = ~0ull;
-    for (int j0 = 0; j0 < n; j0 += KNN_TILE) {
+    const int ld = d + 1;
+    for (int j0 = 0; j0 < n; j0 += TR) {
         __syncthreads();
-        for (int e = threadIdx.x; e < KNN_TILE * d; e += blockDim.x) {
-            const int rr = e / d, t = e % d;
-            tile[rr * (d + 1) + t] = (j0 + rr < n) ? x[(long)(j0 + rr) * xstride + t] : 0.f;
+        for (int rr = warp; rr < TR; rr += KNN_WARPS) {
+            const int j = j0 + rr;
+            for (int t = lane; t < d; t += 32) tile[rr * ld + t] = (j < n) ? x[(long)j * xstride + t] : 0.f;
         }
+        for (int rr = threadIdx.x; rr < TR; rr += blockDim.x) tlab[rr] = (j0 + rr < n) ? label[j0 + rr] : -1;
         __syncthreads();
-        const int j = j0 + lane;
-        if (need && j < n && j != i && label[j] == li) {
-            const float s = sqdist_rn(xi, tile + lane * (d + 1), d);
-            const unsigned long long key = ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j;
-            if (key < L[KNN_K - 1]) {
-                L[KNN_K - 1] = key;
+        if (need) {
+            float sacc[PER_LANE];
 #pragma unroll
-                for (int q = KNN_K - 1; q > 0; --q) {
-                    if (L[q] < L[q - 1]) {
-                        const unsigned long long tmp = L[q];
-                        L[q] = L[q - 1];
-                        L[q - 1] = tmp;
-                    }
+            for (int u = 0; u < PER_LANE; ++u) sacc[u] = 0.f;
+            for (int t = 0; t < d; ++t) {
+                const float a = xi[t];
+#pragma unroll
+                for (int u = 0; u < PER_LANE; ++u) {
+                    const float df = __fsub_rn(a, tile[(lane + 32 * u) * ld + t]);
+                    sacc[u] = __fmaf_rn(df, df, sacc[u]);
                 }
+            }
+#pragma unroll
+            for (int u = 0; u < PER_LANE; ++u) {
+                const int j = j0 + lane + 32 * u;
+                if (j != i && tlab[lane + 32 * u] == li)
+                    knn_insert(L, ((unsigned long long)__float_as_uint(sacc[u]) << 32) | (unsigned)j);
             }
         }
     }
@@ -605,18 +898,32 @@ __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *l
     }
 }
 
-__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn(DevCtx C)
+// shared memory of knn_rows: tile [TR][d+1] | query rows [KNN_WARPS][d] | tile labels [TR]
+__device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+                         float *smem)
+{
+    const int tr = knn_tile_rows(d);
+    float *tile = smem, *xi_s = smem + tr * (d + 1);
+    int *tlab = reinterpret_cast<int *>(xi_s + KNN_WARPS * d);
+    if (tr == 128) knn_rows_t<4>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
+    else if (tr == 64) knn_rows_t<2>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
+    else knn_rows_t<1>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
+}
+
+__global__ void __launch_bounds__(KNN_WARPS * 32, 2) k_knn(DevCtx C, int r0)
 {
     extern __shared__ float ksm[];
-    const int r = blockIdx.y;
+    const int r = r0 + blockIdx.y;
     const RunDesc &D = C.desc[r];
     if (C.state[r].done || !D.clustering) return;
     const int d = D.d;
-    knn_rows(C.fa + D.x_off, D.d_pad, D.n_live, d, C.label + D.pt_off, C.stats[r].n, C.nbr + D.nbr_off * 1, ksm,
-             ksm + KNN_TILE * (d + 1));
+    knn_rows(C.fa + D.x_off, D.d_pad, D.n_live, d, C.label + D.pt_off, C.stats[r].n, C.nbr + D.nbr_off, ksm);
 }
 
-size_t knn_smem_bytes(int d) { return sizeof(float) * ((size_t)KNN_TILE * (d + 1) + (size_t)KNN_WARPS * d); }
+size_t knn_smem_bytes(int d)
+{
+    return sizeof(float) * ((size_t)knn_tile_rows(d) * (d + 2) + (size_t)KNN_WARPS * d);
+}
 
 // Union-find in shared memory: roots are the smallest member index.
 __device__ __forceinline__ int uf_find(volatile int *par, int x)
@@ -754,71 +1061,118 @@ __device__ void stats_split(Stats *st, int p, int np, const int *sz, const int *
 
 constexpr int CL_THREADS = 1024;
 
-__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all)
+__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all, int r0)
 {
     extern __shared__ int csm[];
-    const int r = blockIdx.x;
+    const int r = r0 + blockIdx.x;
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done || !D.clustering) return;
     Stats *st = C.stats + r;
     const int n = D.n_live;
-    int *par = csm;           // [n]
-    int *cnt = csm + n;       // [n]
-    int *newid = csm + 2 * n; // [n]
+    int *par = csm;          // [n] union-find parents, then component roots
+    int *cnt = csm + n;      // [n] component sizes by root, then new ids by root
+    int *lab = csm + 2 * n;  // [n] labels (shared copy)
     __shared__ int s_active[CMAX], s_csize[CMAX], s_merged[CMAX], s_live[1 + CMAX], s_fail;
+    __shared__ int s_nroots[CMAX], s_split[CMAX], s_nsplit;
+    __shared__ int s_roots[CMAX * CMAX];  // ascending roots of the clusters that split
+    __shared__ int s_wsum[CL_THREADS / 32];
     const int tid = threadIdx.x;
     int *label = C.label + D.pt_off;
+    for (int i = tid; i < n; i += blockDim.x) lab[i] = label[i];
     if (tid < CMAX) {
         s_csize[tid] = st->alive[tid] ? st->n[tid] : 0;
         s_active[tid] = st->alive[tid] && st->n[tid] >= 3;
+        s_nroots[tid] = 0;
+        s_split[tid] = 0;
     }
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) {
+        s_fail = 0;
+        s_nsplit = 0;
+    }
     __syncthreads();
-    knn_components_block(C.fa + D.x_off, D.d_pad, n, D.d, label, s_csize, s_active, C.nbr + D.nbr_off, par,
+    knn_components_block(C.fa + D.x_off, D.d_pad, n, D.d, lab, s_csize, s_active, C.nbr + D.nbr_off, par,
                          lastkey_all + D.pt_off, s_merged, s_live);
+    // component sizes and the number of components of every cluster
     for (int i = tid; i < n; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&cnt[par[i]], 1);
+    for (int i = tid; i < n; i += blockDim.x) {
+        atomicAdd(&cnt[par[i]], 1);
+        if (par[i] == i) atomicAdd(&s_nroots[lab[i]], 1);
+    }
     __syncthreads();
+    // clusters that split (ascending id; only clusters present at the start of the iteration)
     if (tid == 0) {
-        // split every cluster with several components, in ascending id order;
-        // parts ordered by their smallest member, part 0 keeps the id, the others
-        // take the lowest free ids (Algorithm 3, eqs. new0-new6)
-        int exists[CMAX];
-        for (int c = 0; c < CMAX; ++c) exists[c] = st->alive[c] && s_csize[c] >= 3;
-        for (int c = 0; c < CMAX && !s_fail; ++c) {
-            if (!exists[c]) continue;
-            int np = 0;
-            int sz[CMAX], ids[CMAX], roots[CMAX];
-            for (int i = 0; i < n && !s_fail; ++i) {
-                if (label[i] == c && par[i] == i) {
-                    if (np == CMAX) {
+        int ns = 0;
+        for (int c = 0; c < CMAX; ++c)
+            if (st->alive[c] && s_csize[c] >= 3 && s_nroots[c] > 1) {
+                if (s_nroots[c] > CMAX) s_fail = 1;
+                s_split[ns++] = c;
+            }
+        s_nsplit = ns;
+    }
+    __syncthreads();
+    const int nsplit = s_nsplit;
+    if (nsplit > 0 && !s_fail) {
+        // ascending roots of each splitting cluster: an ordered block-wide compaction
+        for (int q = 0; q < nsplit; ++q) {
+            const int c = s_split[q];
+            int base = 0;
+            for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+                const int i = i0 + tid;
+                const int f = (i < n && lab[i] == c && par[i] == i) ? 1 : 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                const int lane = tid & 31, warp = tid >> 5;
+                if (lane == 0) s_wsum[warp] = __popc(bal);
+                __syncthreads();
+                int off = base;
+                for (int w2 = 0; w2 < warp; ++w2) off += s_wsum[w2];
+                if (f) {
+                    const int pos = off + __popc(bal & ((1u << lane) - 1u));
+                    if (pos < CMAX) s_roots[q * CMAX + pos] = i;
+                }
+                int tot = 0;
+                for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += s_wsum[w2];
+                __syncthreads();
+                base += tot;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // split in ascending id order: part 0 (smallest member) keeps the id, the
+            // others take the lowest free ids (Algorithm 3, eqs. new0-new6)
+            for (int q = 0; q < nsplit && !s_fail; ++q) {
+                const int c = s_split[q];
+                const int np = s_nroots[c];
+                int sz[CMAX], ids[CMAX];
+                for (int pi = 0; pi < np; ++pi) sz[pi] = cnt[s_roots[q * CMAX + pi]];
+                ids[0] = c;
+                int nxt = 0;
+                for (int pi = 1; pi < np; ++pi) {
+                    while (nxt < CMAX && (st->alive[nxt] || nxt == c)) ++nxt;
+                    if (nxt >= CMAX) {
                         s_fail = 1;
                         break;
                     }
-                    roots[np] = i;
-                    sz[np] = cnt[i];
-                    ++np;
+                    ids[pi] = nxt++;
                 }
+                if (s_fail) break;
+                stats_split(st, c, np, sz, ids);
+                for (int pi = 0; pi < np; ++pi) cnt[s_roots[q * CMAX + pi]] = ids[pi];
             }
-            if (s_fail || np <= 1) continue;
-            ids[0] = c;
-            int nxt = 0;
-            for (int pi = 1; pi < np; ++pi) {
-                while (nxt < CMAX && (st->alive[nxt] || nxt == c)) ++nxt;
-                if (nxt >= CMAX) {
-                    s_fail = 1;
-                    break;
-                }
-                ids[pi] = nxt++;
-            }
-            if (s_fail) break;
-            stats_split(st, c, np, sz, ids);
-            for (int pi = 0; pi < np; ++pi) newid[roots[pi]] = ids[pi];
-            for (int i = 0; i < n; ++i)
-                if (label[i] == c) label[i] = newid[par[i]];
         }
+        __syncthreads();
+        if (!s_fail) {
+            for (int i = tid; i < n; i += blockDim.x) {
+                const int c = lab[i];
+                bool sp = false;
+                for (int q = 0; q < nsplit; ++q) sp |= (s_split[q] == c);
+                if (sp) label[i] = cnt[par[i]];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
         if (s_fail) {
             S->status = NS_ERR_CAPACITY;
             S->done = 1;
@@ -836,13 +1190,13 @@ size_t cluster_smem_bytes(int n_live_max) { return sizeof(int) * 3 * (size_t)n_l
 // ------------------------------------------------------------------------
 // Posterior statistics: H = sum_i p_i (log L_i - log Z), one CTA per run.
 // ------------------------------------------------------------------------
-__global__ void k_info(DevCtx C, int r, double logz, double *out)
+__global__ void k_info(DevCtx C, int r, double logz, double *part)
 {
     const RunDesc &D = C.desc[r];
     const long n = C.state[r].n_dead;
     __shared__ double sh[32], sp[32];
     double h = 0.0, ps = 0.0;
-    for (long i = threadIdx.x; i < n; i += blockDim.x) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const double ll = (double)D.dead_logl[D.dead_off + i];
         const double lp = D.dead_logw[D.dead_off + i] + ll - logz;
         const double p = exp(lp);
@@ -866,8 +1220,8 @@ __global__ void k_info(DevCtx C, int r, double logz, double *out)
             a += sh[w];
             b += sp[w];
         }
-        out[0] = a;
-        out[1] = b;
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
     }
 }
 
@@ -901,7 +1255,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32) k_knn_plain(const float *x, in
                                                               const int *csize, int *nbr)
 {
     extern __shared__ float ksm[];
-    knn_rows(x, d, n, d, label, csize, nbr, ksm, ksm + KNN_TILE * (d + 1));
+    knn_rows(x, d, n, d, label, csize, nbr, ksm);
 }
 
 __global__ void __launch_bounds__(CL_THREADS) k_components_plain(const float *x, int n, int d, const int *label,
@@ -968,45 +1322,56 @@ static cudaError_t set_max_smem(const void *fn, size_t smem)
     return cudaSuccess;
 }
 
-cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem)
+cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem, size_t sort_smem)
 {
     cudaError_t e;
-    if ((e = set_max_smem((const void *)k_select, sel_smem)) != cudaSuccess) return e;
+    if ((e = set_max_smem((const void *)k_sort, sort_smem)) != cudaSuccess) return e;
+    if ((e = set_max_smem((const void *)k_evidence, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_final, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_knn, knn_smem)) != cudaSuccess) return e;
     return set_max_smem((const void *)k_cluster, cl_smem);
 }
 
-cudaError_t launch_select(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s)
+cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
 {
-    k_select<<<n_runs, SEL_THREADS, smem, s>>>(C);
+    k_sort<<<n_runs, SORT_THREADS, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
-cudaError_t launch_final(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s)
+cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
 {
-    k_final<<<n_runs, SEL_THREADS, smem, s>>>(C);
+    k_evidence<<<n_runs, SEL_THREADS, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
-cudaError_t launch_tail(const DevCtx &C, int n_runs, cudaStream_t s)
+cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
 {
-    k_tail<<<n_runs, 256, 0, s>>>(C);
+    k_final<<<n_runs, SEL_THREADS, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
-cudaError_t launch_knn(const DevCtx &C, int n_runs, int max_nlive, size_t smem, cudaStream_t s)
+cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s)
+{
+    k_tail<<<n_runs, 256, 0, s>>>(C, r0);
+    return cudaGetLastError();
+}
+cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s)
 {
     dim3 grid((max_nlive + KNN_WARPS - 1) / KNN_WARPS, n_runs);
-    k_knn<<<grid, KNN_WARPS * 32, smem, s>>>(C);
+    k_knn<<<grid, KNN_WARPS * 32, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
-cudaError_t launch_cluster(const DevCtx &C, int n_runs, unsigned long long *lastkey, size_t smem, cudaStream_t s)
+cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
+                           cudaStream_t s)
 {
-    k_cluster<<<n_runs, CL_THREADS, smem, s>>>(C, lastkey);
+    k_cluster<<<n_runs, CL_THREADS, smem, s>>>(C, lastkey, r0);
     return cudaGetLastError();
 }
+constexpr int INFO_BLOCKS = 152;
 cudaError_t launch_info(const DevCtx &C, int r, double logz, double *out, cudaStream_t s)
 {
-    k_info<<<1, 1024, 0, s>>>(C, r, logz, out);
-    return cudaGetLastError();
+    // out: [2] result followed by [2 * INFO_BLOCKS] partials
+    k_info<<<INFO_BLOCKS, 256, 0, s>>>(C, r, logz, out + 2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce_parts(out + 2, INFO_BLOCKS, 2, out, s);
 }
 cudaError_t launch_export(const DevCtx &C, int r, int d, int d_pad, double logz, double *x, double *logp, long n,
                           cudaStream_t s)

@@ -15,16 +15,20 @@ __host__ __device__ inline Tile tile_of(int id)
 }
 
 size_t select_smem_bytes(int n_live_max);
+size_t sort_smem_bytes(int n_live_max);
 size_t knn_smem_bytes(int d);
 size_t cluster_smem_bytes(int n_live_max);
 size_t evscratch_bytes();
 
-cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem);
-cudaError_t launch_select(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s);
-cudaError_t launch_final(const DevCtx &C, int n_runs, size_t smem, cudaStream_t s);
-cudaError_t launch_tail(const DevCtx &C, int n_runs, cudaStream_t s);
-cudaError_t launch_knn(const DevCtx &C, int n_runs, int max_nlive, size_t smem, cudaStream_t s);
-cudaError_t launch_cluster(const DevCtx &C, int n_runs, unsigned long long *lastkey, size_t smem, cudaStream_t s);
+cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem, size_t sort_smem);
+// run-range launchers: runs r0 .. r0 + n_runs - 1
+cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
+cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s);
+cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
+                           cudaStream_t s);
 cudaError_t launch_info(const DevCtx &C, int r, double logz, double *out, cudaStream_t s);
 cudaError_t launch_export(const DevCtx &C, int r, int d, int d_pad, double logz, double *x, double *logp, long n,
                           cudaStream_t s);

@@ -82,9 +82,59 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
         q = gsum<G>(q);
         return P.b[0] - 0.5f * a * q;
     } else if constexpr (KIND == NS_LIK_MIX_ISO) {
-        // online log-sum-exp over components in chunks of 8 (register-resident)
         constexpr int KC = 8;
         const int K = D.n_comp;
+        if (K <= KC) {
+            // all components in registers: distances, one max, one normalisation
+            float q[KC], tk[KC];
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                q[k] = 0.f;
+                if (k < K) {
+                    const float *mu = P.means + (long)k * dp + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        q[k] = fmaf(r, r, q[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KC; ++k)
+                if (k < K) q[k] = gsum<G>(q[k]);
+            float m = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                tk[k] = (k < K) ? P.b[k] - 0.5f * P.a[k] * q[k] : -INFINITY;
+                m = fmaxf(m, tk[k]);
+            }
+            float s = 0.f;
+            float acc[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = 0.f;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                if (k < K) {
+                    const float wk = expf(tk[k] - m);
+                    s += wk;
+                    if (dmu_w) dmu_w[k] = wk;
+                    const float *mu = P.means + (long)k * dp + c0;
+                    const float c = -wk * P.a[k];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        acc[e] = fmaf(c, r, acc[e]);
+                    }
+                }
+            }
+            const float inv = 1.f / s;
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+            if (dmu_w)
+                for (int k = 0; k < K; ++k) dmu_w[k] *= inv;
+            return m + logf(s);
+        }
+        // more components: online log-sum-exp over chunks of KC
         float m = -INFINITY, s = 0.f;
         float acc[E];
 #pragma unroll
@@ -104,7 +154,8 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                 }
             }
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) q[kk] = gsum<G>(q[kk]);
+            for (int kk = 0; kk < KC; ++kk)
+                if (k0 + kk < K) q[kk] = gsum<G>(q[kk]);
 #pragma unroll
             for (int kk = 0; kk < KC; ++kk) {
                 if (k0 + kk < K) {
@@ -133,7 +184,6 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
 #pragma unroll
         for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
         if (dmu_w) {
-            // responsibilities needed by the parameter adjoint: recompute per component
             for (int k = 0; k < K; ++k) {
                 const float *mu = P.means + (long)k * dp + c0;
                 float qk = 0.f;
@@ -447,6 +497,11 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 
         // ---- one step of Algorithm 5 for every stepping walker of the warp
         const int ts = t + 1;
+        // this step's random numbers depend only on (slot, step): draw them first
+        uint32_t spare = 0;
+        lane_normals<E>(D, iter, P_NOISE, w, ts, c0, eps, &spare);
+        // the reservoir word: spare bits of the walker's noise block 0 (held by its lane 0)
+        const uint32_t res_word = __shfl_sync(0xffffffffu, spare, gbase);
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
@@ -465,15 +520,17 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         outbox = gsum_i<G>(outbox);
         const bool outside = (outbox > 0) || !(ll > lstar);
         float pnb = 0.f, pg = 0.f, gg = 0.f;
+        if (__any_sync(0xffffffffu, stepping && outside)) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            pnb = fmaf(p[e], nb[e], pnb);
-            pg = fmaf(p[e], g[e], pg);
-            gg = fmaf(g[e], g[e], gg);
+            for (int e = 0; e < E; ++e) {
+                pnb = fmaf(p[e], nb[e], pnb);
+                pg = fmaf(p[e], g[e], pg);
+                gg = fmaf(g[e], g[e], gg);
+            }
+            pnb = gsum<G>(pnb);
+            pg = gsum<G>(pg);
+            gg = gsum<G>(gg);
         }
-        pnb = gsum<G>(pnb);
-        pg = gsum<G>(pg);
-        gg = gsum<G>(gg);
         if (stepping && outside) {
             if (outbox > 0) {
                 // reflect off the violated prior-box faces: n = nb / sqrt(#faces)
@@ -491,7 +548,6 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
             }
         }
         // momentum noise
-        lane_normals<E>(D, iter, P_NOISE, w, ts, c0, eps);
         if (stepping) {
             if (D.noise_mode == 1) {
 #pragma unroll
@@ -505,15 +561,9 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         }
         // trajectory preservation: size-1 reservoir over the saved inside states
         const bool save = stepping && !outside && (ts >= t_save);
-        int acc = 0;
-        if (save && lig == 0) {
-            const U4 rw = rng_block(D, iter, P_RES, w, ts, 0);
-            acc = ((static_cast<uint64_t>(rw.x) * static_cast<uint64_t>(count + 1)) >> 32) == 0;
-        }
-        acc = __shfl_sync(0xffffffffu, acc, gbase);
         if (save) {
             ++count;
-            if (acc) {
+            if (((static_cast<uint64_t>(res_word) * static_cast<uint64_t>(count)) >> 32) == 0) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) xr[e] = x[e];
                 res_ll = ll;

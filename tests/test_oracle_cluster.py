@@ -15,9 +15,10 @@ def _scipy_alg4(x):
     if m < 3:
         return np.arange(m) * 0
     dist = np.zeros((m, m), np.float32)
-    for t in range(x.shape[1]):  # sequential FP32 accumulation in coordinate order
+    for t in range(x.shape[1]):  # FP32 fused multiply-add per coordinate, in coordinate order
         diff = (x[:, None, t] - x[None, :, t]).astype(np.float32)
-        dist = (dist + (diff * diff).astype(np.float32)).astype(np.float32)
+        # fmaf(diff, diff, dist): the product of two FP32 values is exact in FP64
+        dist = (diff.astype(np.float64) * diff.astype(np.float64) + dist.astype(np.float64)).astype(np.float32)
     order = []
     for i in range(m):
         js = [j for j in range(m) if j != i]
