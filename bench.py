@@ -39,6 +39,11 @@ UNIT = "point-steps/s"
 WORKLOAD = "c2"
 DEFAULT_REPLICAS = 17
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) per k_hss launch from one ncu capture of this workload
+# (profiles/k_hss_c2x17.md), valid only for the kernel sources with these hashes.
+HSS_TRAFFIC_BYTES = 3.364e6
+HSS_TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "88ed08405d6fdc41",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "f19a947a9ee78cc9"}
 SMS = 152
 FP32_LANES_PER_SM = 128
 
@@ -117,6 +122,16 @@ class ClockSampler:
 def replicas(R: int, rank: int):
     w = W.workload(WORKLOAD)
     return w, [dict(w, cfg=dict(w["cfg"], run_id=rank * R + r)) for r in range(R)]
+
+
+def measured_traffic():
+    """The profiled traffic per launch, or None once the kernel sources differ from the profiled ones."""
+    import hashlib
+    for rel, h in HSS_TRAFFIC_SOURCES.items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
+                return None
+    return HSS_TRAFFIC_BYTES
 
 
 def load_peaks():
@@ -277,7 +292,8 @@ def gpu_arm(args):
     peak = SMS * FP32_LANES_PER_SM * f_sm
     hss_iters = max(prof["hss_iters"], 1)
     roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
-            "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(),
+            "traffic_unit": "bytes per launch (DRAM read + write)",
             "kernel": "k_hss (phases 0-2)", "ops_per_point_step": ops,
             "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
