@@ -282,7 +282,7 @@ def gpu_arm(args):
         tot_pts = float(tp.item())
     value = tot_pts / sum(times)
     ms = 1000.0 * sum(times) / len(times)
-    # roofline of the dominant kernel (the three HSS phases): algorithmic lane-ops / HSS time
+    # roofline of the dominant kernel (HSS): algorithmic lane-ops / HSS time
     zall = np.array(logz)
     out_frac_est = 0.12
     ops = lane_ops_per_point_step(32, 4, out_frac_est)
@@ -294,7 +294,8 @@ def gpu_arm(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
             "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(),
             "traffic_unit": "bytes per launch (DRAM read + write)",
-            "kernel": "k_hss (phases 0-2)", "ops_per_point_step": ops,
+            "kernel": ("k_hss1 + k_hss_pick (single pass)" if prof.get("rec_len", 0) > 0 else "k_hss (phases 0-2)"),
+            "hss_rec_overflows": prof.get("rec_overflows"), "ops_per_point_step": ops,
             "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
             "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}

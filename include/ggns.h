@@ -137,12 +137,15 @@ ns_status ns_run(ns_ctx *ctx, long max_iters);
  * Used to repeat a workload without allocating.  Synchronises. */
 ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
 
-/* Profiling counters of ctx (out[5]): out[0] milliseconds during which at
+/* Profiling counters of ctx (out[7]): out[0] milliseconds during which at
  * least one HSS kernel of ns_run was executing (union over the run groups of
- * the intervals between CUDA events recorded around the three HSS phases of
- * each iteration), out[1] group-iterations measured, out[2] kernels launched by
+ * the intervals between CUDA events recorded around the HSS kernels of each
+ * iteration), out[1] group-iterations measured, out[2] kernels launched by
  * ctx, out[3] rounds of graph replays, out[4] the summed (not merged) HSS
- * intervals.  reset != 0 zeroes them after reading. */
+ * intervals, out[5] iterations (summed over runs, since the last restart) whose
+ * single-pass HSS ran out of step records and was redone in three phases,
+ * out[6] step records per walker (0: the three-phase form only).  reset != 0
+ * zeroes out[0..4] after reading.  Synchronises. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 
 typedef struct {

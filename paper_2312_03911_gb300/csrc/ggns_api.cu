@@ -59,6 +59,7 @@ struct RunClass {
     int max_k = 0, max_n = 0;
     size_t smem = 0;
     int prec_in_smem = 0;
+    int single = 0;  // HSS in one pass (every walker block resident at once)
 };
 
 // Runs advanced together by one CUDA graph on one stream.  Different groups
@@ -118,6 +119,10 @@ struct ns_ctx {
     cudaEvent_t ev[GRAPH_ITERS][2] = {};
     double hss_ms = 0.0;
     long hss_iters = 0, launches = 0, replays = 0;
+    // single-pass HSS records (one row per walker-step, rec_len rows per walker)
+    RecView rec{};
+    long *rec_base_dev = nullptr;
+    int hss_mode = 0;  // 0 automatic, 1 single pass where resident, 3 always three phases
     int launches_per_iter = 0;
     // scratch for the posterior kernels (grown on demand, reused)
     double *scratch = nullptr;
@@ -355,10 +360,24 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
     CU(cudaEventRecord(g.join_ev, g.ev_stream));
     ++n;
     if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][0], s, cudaEventRecordExternal));
+    // single pass where every walker block of the class is resident, then the
+    // three phases (for single-pass classes only if the records overflowed)
+    for (auto &cl : g.classes)
+        if (cl.single) {
+            CU(kind_launch(cl.kind).hss1(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
+                                         ctx->rec_base_dev, cl.smem, cl.prec_in_smem, s));
+            ++n;
+        }
+    for (auto &cl : g.classes)
+        if (cl.single) {
+            CU(kind_launch(cl.kind).pick(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
+                                         ctx->rec_base_dev, s));
+            ++n;
+        }
     for (int phase = 0; phase < 3; ++phase)
         for (auto &cl : g.classes) {
-            CU(kind_launch(cl.kind).hss(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, phase, cl.smem,
-                                        cl.prec_in_smem, s));
+            CU(kind_launch(cl.kind).hss(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k,
+                                        cl.single ? (phase | 4) : phase, cl.smem, cl.prec_in_smem, s));
             ++n;
         }
     if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][1], s, cudaEventRecordExternal));
@@ -640,6 +659,50 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         };
         CK(setup_cls());
     }
+    // single-pass HSS records: GGNS_HSS = 3 keeps the three-phase form, GGNS_REC_LEN
+    // sets the records per walker (default 256, bounded by n_steps and a 4 GiB budget)
+    int n_sm = 0;
+    auto smq = [&]() -> ns_status {
+        CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+        return NS_OK;
+    };
+    CK(smq());
+    {
+        if (const char *v = getenv("GGNS_HSS")) ctx->hss_mode = atoi(v);
+        long rec_len = 256;
+        if (const char *v = getenv("GGNS_REC_LEN")) rec_len = std::max(1, atoi(v));
+        int max_steps = 0, xs = 0;
+        long walkers = 0;
+        for (int r = 0; r < n_runs; ++r) {
+            max_steps = std::max(max_steps, cfg[r].n_steps);
+            xs = std::max(xs, ctx->desc[r].d_pad);
+            walkers += ctx->desc[r].k;
+        }
+        rec_len = std::min<long>(rec_len, max_steps);
+        const long budget = 4l << 30;
+        const long row_bytes = (long)xs * 4 + 12;
+        while (rec_len > 16 && walkers * rec_len * row_bytes > budget) rec_len /= 2;
+        if (ctx->hss_mode != 3 && walkers * rec_len * row_bytes <= budget) {
+            auto mkrec = [&]() -> ns_status {
+                const long rows = walkers * rec_len;
+                CU(cudaMalloc(&ctx->rec.meta, sizeof(uint2) * rows));
+                CU(cudaMalloc(&ctx->rec.ll, sizeof(float) * rows));
+                CU(cudaMalloc(&ctx->rec.x, sizeof(float) * rows * xs));
+                std::vector<long> base(n_runs);
+                long acc = 0;
+                for (int r = 0; r < n_runs; ++r) {
+                    base[r] = acc;
+                    acc += (long)ctx->desc[r].k * rec_len;
+                }
+                CU(cudaMalloc(&ctx->rec_base_dev, sizeof(long) * n_runs));
+                CU(cudaMemcpy(ctx->rec_base_dev, base.data(), sizeof(long) * n_runs, cudaMemcpyHostToDevice));
+                ctx->rec.rec_len = (int)rec_len;
+                ctx->rec.xs = xs;
+                return NS_OK;
+            };
+            CK(mkrec());
+        }
+    }
     // run groups: one stream and one graph each (GGNS_RUNS_PER_GROUP runs; default: all runs in one group)
     {
         int per = n_runs;
@@ -672,6 +735,14 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 for (auto &rc : g.classes) {
                     CU(cudaMalloc(&rc.runs_dev, sizeof(int) * rc.runs.size()));
                     CU(cudaMemcpy(rc.runs_dev, rc.runs.data(), sizeof(int) * rc.runs.size(), cudaMemcpyHostToDevice));
+                    rc.single = 0;
+                    if (ctx->rec.rec_len > 0) {
+                        int per_sm = 0;
+                        CU(kind_launch(rc.kind).hss1_occ(rc.tile, rc.smem, &per_sm));
+                        const long gpc = HSS_THREADS / tile_of(rc.tile).g;
+                        const long blocks = (rc.max_k + gpc - 1) / gpc * (long)rc.runs.size();
+                        rc.single = blocks <= (long)per_sm * n_sm ? 1 : 0;
+                    }
                 }
                 CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
                 CU(cudaStreamCreateWithFlags(&g.ev_stream, cudaStreamNonBlocking));
@@ -859,6 +930,13 @@ ns_status ns_profile(const ns_ctx *cctx, double *out, int reset)
     out[2] = (double)ctx->launches;
     out[3] = (double)ctx->replays;
     out[4] = ctx->hss_ms_sum;
+    std::vector<RunState> st;
+    ns_status rs = read_states(ctx, st);
+    if (rs != NS_OK) return rs;
+    long over = 0;
+    for (auto &x : st) over += x.n_rec_overflow;
+    out[5] = (double)over;
+    out[6] = ctx->rec.rec_len;
     if (reset) {
         ctx->hss_ms = ctx->hss_ms_sum = 0.0;
         ctx->hss_iters = ctx->launches = ctx->replays = 0;
@@ -1097,6 +1175,10 @@ void ns_destroy(ns_ctx *ctx)
         for (int j = 0; j < 2; ++j)
             if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->rec.meta) cudaFree(ctx->rec.meta);
+    if (ctx->rec.ll) cudaFree(ctx->rec.ll);
+    if (ctx->rec.x) cudaFree(ctx->rec.x);
+    if (ctx->rec_base_dev) cudaFree(ctx->rec_base_dev);
     if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
     delete ctx;
 }
@@ -1213,6 +1295,7 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
     S.dt = dt;
     S.lstar = lstar;
     S.n_dead = n;
+    S.remain_min = S.remain_max = (int)n;
     const int zr = 0;
     CU(cudaMemcpyAsync(runs, &zr, sizeof(int), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(ddesc, &D, sizeof D, cudaMemcpyHostToDevice, s));
@@ -1236,8 +1319,33 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         for (int r : ctx->classes[i].runs)
             if (r == 0) cls = i;
     const RunClass &rc = ctx->classes[cls];
+    // the single-pass form where the context uses it and all n walkers are resident
+    RecView R{};
+    long *rbase = nullptr;
+    int single = 0;
+    if (ctx->rec.rec_len > 0) {
+        int per_sm = 0, n_sm = 0;
+        CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+        CU(kind_launch(D.kind).hss1_occ(D.tile, rc.smem, &per_sm));
+        const long gpc = HSS_THREADS / tile_of(D.tile).g;
+        single = (n + gpc - 1) / gpc <= (long)per_sm * n_sm ? 1 : 0;
+    }
+    if (single) {
+        R.rec_len = std::min(ctx->rec.rec_len, D.n_steps);
+        R.xs = dp;
+        const long rows = n * (long)R.rec_len;
+        const long zero_base = 0;
+        CU(cudaMalloc(&R.meta, sizeof(uint2) * rows));
+        CU(cudaMalloc(&R.ll, sizeof(float) * rows));
+        CU(cudaMalloc(&R.x, sizeof(float) * rows * dp));
+        CU(cudaMalloc(&rbase, sizeof(long)));
+        CU(cudaMemcpyAsync(rbase, &zero_base, sizeof(long), cudaMemcpyHostToDevice, s));
+        CU(kind_launch(D.kind).hss1(D.tile, C, runs, 1, (int)n, R, rbase, rc.smem, rc.prec_in_smem, s));
+        CU(kind_launch(D.kind).pick(D.tile, C, runs, 1, (int)n, R, rbase, s));
+    }
     for (int phase = 0; phase < 3; ++phase)
-        CU(kind_launch(D.kind).hss(D.tile, C, runs, 1, (int)n, phase, rc.smem, rc.prec_in_smem, s));
+        CU(kind_launch(D.kind).hss(D.tile, C, runs, 1, (int)n, single ? (phase | 4) : phase, rc.smem,
+                                   rc.prec_in_smem, s));
     CU(cudaMemcpy2DAsync(x_out_dev, sizeof(float) * d, fa + (long)n * dp, sizeof(float) * dp, sizeof(float) * d, n,
                          cudaMemcpyDeviceToDevice, s));
     CU(cudaMemcpyAsync(logl_out_dev, logl + n, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
@@ -1253,7 +1361,8 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         stats_host[2] = S.t_save;
         stats_host[3] = S.t_stop;
     }
-    void *ptrs[] = {fa, logl, lab, order, start, nlab, wint, wres, dx, dl, dw, dlab, runs, ddesc, dstate};
+    void *ptrs[] = {fa, logl, lab, order, start, nlab, wint, wres, dx, dl, dw, dlab, runs, ddesc, dstate,
+                    R.meta, R.ll, R.x, rbase};
     for (void *p : ptrs) cudaFree(p);
     return NS_OK;
 }

@@ -88,6 +88,12 @@ struct RunState {
     double logz, logz2;
     long dead_base;        // first dead row of the current iteration's kills
     int ev_pending;        // the iteration's statistics update has not run yet
+    int remain_min;        // single-pass HSS: walkers yet to reach min_ref
+    int remain_max;        // single-pass HSS: walkers yet to meet their stop rule
+    int rec_overflow;      // single-pass HSS ran out of record length: redo in three phases
+    unsigned int wcount1;  // single-pass HSS walker refill counter
+    int t_save1, t_stop1;  // single-pass HSS window
+    int n_rec_overflow;    // iterations redone in three phases
     int kill_cnt[CMAX];    // kills per cluster in the current iteration
     int spawn_cnt[CMAX];   // new points per cluster in the current iteration
 };

@@ -672,6 +672,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
         S->t_stop = 0;
         S->n_in = 0;
         S->n_out = 0;
+        S->wcount1 = 0;
+        S->t_save1 = 0;
+        S->t_stop1 = 0;
+        S->remain_min = k;
+        S->remain_max = k;
+        S->rec_overflow = 0;
     }
 }
 
@@ -775,6 +781,7 @@ __global__ void k_tail(DevCtx C, int r0)
     else if (out_frac < D.out_lo) S->dt *= 1.1;
     S->n_like += (long)D.k * S->t_stop;
     S->n_steps_total += (long)D.k * S->t_stop;
+    S->n_rec_overflow += S->rec_overflow;
     if (S->log_xl > S->log_xl_max) S->log_xl_max = S->log_xl;
     bool stop;
     if (D.termination == 0) {
@@ -801,23 +808,14 @@ __global__ void k_tail(DevCtx C, int r0)
 // Cluster finding (Algorithm 4)
 // ------------------------------------------------------------------------
 // k-NN ranks 1..KNN_K of point i among the points with the same label, by
-// ascending (FP32 squared distance, index); the distance is accumulated in
-// coordinate order with round-to-nearest and no contraction.
-constexpr int KNN_WARPS = 16;
-
-__host__ __device__ __forceinline__ int knn_tile_rows(int d) { return d < 64 ? 128 : (d < 128 ? 64 : 32); }
-
-// Squared distance in coordinate order: each squared difference is added with
-// a correctly rounded fused multiply-add (the oracle uses C's fmaf).
-__device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d)
-{
-    float s = 0.f;
-    for (int t = 0; t < d; ++t) {
-        const float df = __fsub_rn(a[t], b[t]);
-        s = __fmaf_rn(df, df, s);
-    }
-    return s;
-}
+// ascending (FP32 squared distance, index).
+// k-NN ranks, one query per lane: a CTA of KQ_WARPS warps serves 32 queries; warp w
+// scans the candidates j = w, w + KQ_WARPS, ...  Every lane reads the same candidate
+// row (a broadcast load), so the distance of one (query, candidate) pair costs a
+// quarter of a float4 load, one subtraction and one fused multiply-add per
+// coordinate.  Each lane keeps the exact top KNN_K of its candidates; the warps'
+// lists are merged through shared memory at the end.
+constexpr int KQ_WARPS = 4;
 
 __device__ __forceinline__ void knn_insert(unsigned long long (&L)[KNN_K], unsigned long long key)
 {
@@ -834,83 +832,180 @@ __device__ __forceinline__ void knn_insert(unsigned long long (&L)[KNN_K], unsig
     }
 }
 
-// One warp per query point; the candidates stream through shared memory in
-// tiles of knn_tile_rows(d) rows, each lane scoring TR/32 of them per tile with
-// independent accumulation chains.
-template <int PER_LANE>
-__device__ void knn_rows_t(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
-                           float *tile, float *xi_s, int *tlab)
+// Squared distance in coordinate order: each squared difference is added with
+// a correctly rounded fused multiply-add (the oracle uses C's fmaf).
+__device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d)
 {
-    constexpr int TR = 32 * PER_LANE;
+    float s = 0.f;
+    for (int t = 0; t < d; ++t) {
+        const float df = __fsub_rn(a[t], b[t]);
+        s = __fmaf_rn(df, df, s);
+    }
+    return s;
+}
+
+// QR: query components held in registers (d <= QR, QR a multiple of 4).  The
+// candidates stream through shared memory in tiles of KQ_TILE rows (coalesced
+// loads by the whole CTA); every lane of a warp then reads the same row (a
+// broadcast), two candidates at a time for independent accumulation chains.
+constexpr int KQ_TILE = 128;
+
+template <int QR>
+__device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+                          unsigned long long *merge /* [KQ_WARPS][32][KNN_K] */, float *tile /* [KQ_TILE][QR] */,
+                          int *tlab /* [KQ_TILE] */)
+{
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * KNN_WARPS + warp;
+    const int i = blockIdx.x * 32 + lane;
     const bool act = i < n;
     const int li = act ? label[i] : -1;
     const bool need = act && csize[li] >= 3;
-    float *xi = xi_s + warp * d;
-    if (act)
-        for (int t = lane; t < d; t += 32) xi[t] = x[(long)i * xstride + t];
+    const bool any_need = __syncthreads_or(need);
+    float q[QR];
+#pragma unroll
+    for (int t = 0; t < QR; ++t) q[t] = (act && t < d) ? x[(long)i * xstride + t] : 0.f;
     unsigned long long L[KNN_K];
 #pragma unroll
-    for (int q = 0; q < KNN_K; ++q) L[q] = ~0ull;
-    const int ld = d + 1;
-    for (int j0 = 0; j0 < n; j0 += TR) {
-        __syncthreads();
-        for (int rr = warp; rr < TR; rr += KNN_WARPS) {
-            const int j = j0 + rr;
-            for (int t = lane; t < d; t += 32) tile[rr * ld + t] = (j < n) ? x[(long)j * xstride + t] : 0.f;
+    for (int u = 0; u < KNN_K; ++u) L[u] = ~0ull;
+    if (any_need) {
+        for (int j0 = 0; j0 < n; j0 += KQ_TILE) {
+            __syncthreads();
+            // rows padded with zeros up to QR (the query is zero there too)
+            for (int e = threadIdx.x; e < KQ_TILE * (QR / 4); e += blockDim.x) {
+                const int rr = e / (QR / 4), t4 = (e - rr * (QR / 4)) * 4;
+                const int j = j0 + rr;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j < n) {
+                    const float *row = x + (long)j * xstride;
+                    if (t4 + 0 < d) v.x = row[t4 + 0];
+                    if (t4 + 1 < d) v.y = row[t4 + 1];
+                    if (t4 + 2 < d) v.z = row[t4 + 2];
+                    if (t4 + 3 < d) v.w = row[t4 + 3];
+                }
+                *reinterpret_cast<float4 *>(tile + rr * QR + t4) = v;
+            }
+            for (int rr = threadIdx.x; rr < KQ_TILE; rr += blockDim.x) tlab[rr] = (j0 + rr < n) ? label[j0 + rr] : -1;
+            __syncthreads();
+            const int rows = min(KQ_TILE, n - j0);
+            for (int rr = warp * 2; rr < rows; rr += 2 * KQ_WARPS) {
+                const float *ra = tile + rr * QR;
+                const float *rb = tile + (rr + 1) * QR;  // inside the tile (zeros past n)
+                float sa = 0.f, sb = 0.f;
+#pragma unroll
+                for (int t = 0; t < QR; t += 4) {
+                    const float4 va = *reinterpret_cast<const float4 *>(ra + t);
+                    const float4 vb = *reinterpret_cast<const float4 *>(rb + t);
+                    float da = __fsub_rn(q[t], va.x), db = __fsub_rn(q[t], vb.x);
+                    sa = __fmaf_rn(da, da, sa);
+                    sb = __fmaf_rn(db, db, sb);
+                    da = __fsub_rn(q[t + 1], va.y);
+                    db = __fsub_rn(q[t + 1], vb.y);
+                    sa = __fmaf_rn(da, da, sa);
+                    sb = __fmaf_rn(db, db, sb);
+                    da = __fsub_rn(q[t + 2], va.z);
+                    db = __fsub_rn(q[t + 2], vb.z);
+                    sa = __fmaf_rn(da, da, sa);
+                    sb = __fmaf_rn(db, db, sb);
+                    da = __fsub_rn(q[t + 3], va.w);
+                    db = __fsub_rn(q[t + 3], vb.w);
+                    sa = __fmaf_rn(da, da, sa);
+                    sb = __fmaf_rn(db, db, sb);
+                }
+                const int ja = j0 + rr, jb = ja + 1;
+                if (need && tlab[rr] == li && ja != i) knn_insert(L, ((unsigned long long)__float_as_uint(sa) << 32) | (unsigned)ja);
+                if (need && rr + 1 < rows && tlab[rr + 1] == li && jb != i)
+                    knn_insert(L, ((unsigned long long)__float_as_uint(sb) << 32) | (unsigned)jb);
+            }
         }
-        for (int rr = threadIdx.x; rr < TR; rr += blockDim.x) tlab[rr] = (j0 + rr < n) ? label[j0 + rr] : -1;
-        __syncthreads();
-        if (need) {
-            float sacc[PER_LANE];
+    }
 #pragma unroll
-            for (int u = 0; u < PER_LANE; ++u) sacc[u] = 0.f;
-            for (int t = 0; t < d; ++t) {
-                const float a = xi[t];
+    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KNN_K + u] = L[u];
+    __syncthreads();
+    if (warp == 0) {
+        // merge the KQ_WARPS sorted lists of this lane's query
+        int pos[KQ_WARPS];
 #pragma unroll
-                for (int u = 0; u < PER_LANE; ++u) {
-                    const float df = __fsub_rn(a, tile[(lane + 32 * u) * ld + t]);
-                    sacc[u] = __fmaf_rn(df, df, sacc[u]);
+        for (int w2 = 0; w2 < KQ_WARPS; ++w2) pos[w2] = 0;
+        for (int rnk = 0; rnk < KNN_K; ++rnk) {
+            unsigned long long best = ~0ull;
+            int bw = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
+                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KNN_K + pos[w2]] : ~0ull;
+                if (v < best) {
+                    best = v;
+                    bw = w2;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < PER_LANE; ++u) {
-                const int j = j0 + lane + 32 * u;
-                if (j != i && tlab[lane + 32 * u] == li)
-                    knn_insert(L, ((unsigned long long)__float_as_uint(sacc[u]) << 32) | (unsigned)j);
-            }
+            for (int w2 = 0; w2 < KQ_WARPS; ++w2)
+                if (w2 == bw) ++pos[w2];
+            if (act) nbr[(long)i * KNN_K + rnk] = (best == ~0ull) ? -1 : (int)(best & 0xffffffffu);
         }
-    }
-    // warp merge of the 32 sorted lists
-    for (int rnk = 0; rnk < KNN_K; ++rnk) {
-        unsigned long long mn = L[0];
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mn, o);
-            mn = v < mn ? v : mn;
-        }
-        if (L[0] == mn && mn != ~0ull) {
-#pragma unroll
-            for (int q = 0; q < KNN_K - 1; ++q) L[q] = L[q + 1];
-            L[KNN_K - 1] = ~0ull;
-        }
-        if (act && lane == 0) nbr[(long)i * KNN_K + rnk] = (mn == ~0ull) ? -1 : (int)(mn & 0xffffffffu);
     }
 }
 
-// shared memory of knn_rows: tile [TR][d+1] | query rows [KNN_WARPS][d] | tile labels [TR]
+// Queries wider than the register budget: the query row is read from global memory.
+__device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+                               unsigned long long *merge)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 32 + lane;
+    const bool act = i < n;
+    const int li = act ? label[i] : -1;
+    const bool need = act && csize[li] >= 3;
+    const float *qi = x + (long)(act ? i : 0) * xstride;
+    unsigned long long L[KNN_K];
+#pragma unroll
+    for (int u = 0; u < KNN_K; ++u) L[u] = ~0ull;
+    if (__any_sync(0xffffffffu, need)) {
+        for (int j = warp; j < n; j += KQ_WARPS) {
+            const int lj = label[j];
+            const float s = sqdist_rn(qi, x + (long)j * xstride, d);
+            if (need && lj == li && j != i) knn_insert(L, ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KNN_K + u] = L[u];
+    __syncthreads();
+    if (warp == 0) {
+        int pos[KQ_WARPS];
+#pragma unroll
+        for (int w2 = 0; w2 < KQ_WARPS; ++w2) pos[w2] = 0;
+        for (int rnk = 0; rnk < KNN_K; ++rnk) {
+            unsigned long long best = ~0ull;
+            int bw = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
+                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KNN_K + pos[w2]] : ~0ull;
+                if (v < best) {
+                    best = v;
+                    bw = w2;
+                }
+            }
+#pragma unroll
+            for (int w2 = 0; w2 < KQ_WARPS; ++w2)
+                if (w2 == bw) ++pos[w2];
+            if (act) nbr[(long)i * KNN_K + rnk] = (best == ~0ull) ? -1 : (int)(best & 0xffffffffu);
+        }
+    }
+}
+
+// shared memory: merge lists [KQ_WARPS][32][KNN_K] u64 | tile [KQ_TILE][64] f32 | tile labels [KQ_TILE]
 __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
                          float *smem)
 {
-    const int tr = knn_tile_rows(d);
-    float *tile = smem, *xi_s = smem + tr * (d + 1);
-    int *tlab = reinterpret_cast<int *>(xi_s + KNN_WARPS * d);
-    if (tr == 128) knn_rows_t<4>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
-    else if (tr == 64) knn_rows_t<2>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
-    else knn_rows_t<1>(x, xstride, n, d, label, csize, nbr, tile, xi_s, tlab);
+    unsigned long long *merge = reinterpret_cast<unsigned long long *>(smem);
+    float *tile = reinterpret_cast<float *>(merge + KQ_WARPS * 32 * KNN_K);
+    int *tlab = reinterpret_cast<int *>(tile + KQ_TILE * 64);
+    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
+    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
+    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
+    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
+    else knn_lanes_wide(x, xstride, n, d, label, csize, nbr, merge);
 }
 
-__global__ void __launch_bounds__(KNN_WARPS * 32, 2) k_knn(DevCtx C, int r0)
+__global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
 {
     extern __shared__ float ksm[];
     const int r = r0 + blockIdx.y;
@@ -922,7 +1017,9 @@ __global__ void __launch_bounds__(KNN_WARPS * 32, 2) k_knn(DevCtx C, int r0)
 
 size_t knn_smem_bytes(int d)
 {
-    return sizeof(float) * ((size_t)knn_tile_rows(d) * (d + 2) + (size_t)KNN_WARPS * d);
+    (void)d;
+    return sizeof(unsigned long long) * (size_t)KQ_WARPS * 32 * KNN_K + sizeof(float) * KQ_TILE * 64 +
+           sizeof(int) * KQ_TILE;
 }
 
 // Union-find in shared memory: roots are the smallest member index.
@@ -1251,7 +1348,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sort_logl(const float *logl, in
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(skeys[i] & 0xffffffffu);
 }
 
-__global__ void __launch_bounds__(KNN_WARPS * 32) k_knn_plain(const float *x, int n, int d, const int *label,
+__global__ void __launch_bounds__(KQ_WARPS * 32) k_knn_plain(const float *x, int n, int d, const int *label,
                                                               const int *csize, int *nbr)
 {
     extern __shared__ float ksm[];
@@ -1354,8 +1451,8 @@ cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s)
 }
 cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s)
 {
-    dim3 grid((max_nlive + KNN_WARPS - 1) / KNN_WARPS, n_runs);
-    k_knn<<<grid, KNN_WARPS * 32, smem, s>>>(C, r0);
+    dim3 grid((max_nlive + 31) / 32, n_runs);
+    k_knn<<<grid, KQ_WARPS * 32, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
 cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
@@ -1407,7 +1504,7 @@ cudaError_t launch_knn_components(const float *x, int n, int d, const int *label
     const size_t ks = knn_smem_bytes(d);
     cudaError_t e = set_max_smem((const void *)k_knn_plain, ks);
     if (e != cudaSuccess) return e;
-    k_knn_plain<<<(n + KNN_WARPS - 1) / KNN_WARPS, KNN_WARPS * 32, ks, s>>>(x, n, d, label, csize, nbr);
+    k_knn_plain<<<(n + 31) / 32, KQ_WARPS * 32, ks, s>>>(x, n, d, label, csize, nbr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t cs = sizeof(int) * (size_t)n;

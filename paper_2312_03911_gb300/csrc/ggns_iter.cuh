@@ -45,6 +45,7 @@ cudaError_t launch_stats_plain(Stats *st, double *zz, int k, const double *kL, c
 void set_global_error(const char *msg);
 
 // per likelihood kind (ggns_k_<kind>.cu)
+struct RecView;
 struct KindLaunch {
     cudaError_t (*prior)(int tile, const DevCtx &C, const int *runs, int nr, int max_n, size_t smem, int pis,
                          cudaStream_t s);
@@ -55,6 +56,11 @@ struct KindLaunch {
     cudaError_t (*grad_means)(int tile, const DevCtx &C, int run, double logz, double *part, int n_blocks,
                               size_t smem, int pis, cudaStream_t s);
     cudaError_t (*set_smem)(int tile, size_t smem);
+    cudaError_t (*hss1)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                        const long *rec_base, size_t smem, int pis, cudaStream_t s);
+    cudaError_t (*pick)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                        const long *rec_base, cudaStream_t s);
+    cudaError_t (*hss1_occ)(int tile, size_t smem, int *blocks_per_sm);
 };
 const KindLaunch &kind_launch(int kind);
 

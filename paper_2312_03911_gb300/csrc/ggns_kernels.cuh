@@ -75,7 +75,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
         float q = 0.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const float r = (c0 + e < d) ? x[e] - P.means[c0 + e] : 0.f;
+            const float r = x[e] - P.means[c0 + e];  // padded components: x = mu = 0
             q = fmaf(r, r, q);
             g[e] = -a * r;
         }
@@ -94,7 +94,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                     const float *mu = P.means + (long)k * dp + c0;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        const float r = x[e] - mu[e];
                         q[k] = fmaf(r, r, q[k]);
                     }
                 }
@@ -122,7 +122,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                     const float c = -wk * P.a[k];
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        const float r = x[e] - mu[e];
                         acc[e] = fmaf(c, r, acc[e]);
                     }
                 }
@@ -148,7 +148,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                     const float *mu = P.means + (long)(k0 + kk) * dp + c0;
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        const float r = x[e] - mu[e];
                         q[kk] = fmaf(r, r, q[kk]);
                     }
                 }
@@ -174,7 +174,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                     const float ak = P.a[k];
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                        const float r = x[e] - mu[e];
                         acc[e] = fmaf(-wk * ak, r, acc[e]);
                     }
                 }
@@ -189,7 +189,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
                 float qk = 0.f;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const float r = (c0 + e < d) ? x[e] - mu[e] : 0.f;
+                    const float r = x[e] - mu[e];
                     qk = fmaf(r, r, qk);
                 }
                 qk = gsum<G>(qk);
@@ -249,9 +249,9 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
             float q = 0.f;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const float r = (c0 + e < d) ? x[e] - P.means[c0 + e] : 0.f;
+                const float r = x[e] - P.means[c0 + e];
                 q = fmaf(r, y[e], q);
-                g[e] = (c0 + e < d) ? -y[e] : 0.f;
+                g[e] = -y[e];
             }
             q = gsum<G>(q);
             if (dmu_w) dmu_w[0] = 1.f;
@@ -266,9 +266,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
             const float *pm = P.pmu + (long)k * dp + c0;
             float q = 0.f;
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (c0 + e < d) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
-            }
+            for (int e = 0; e < E; ++e) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
             q = gsum<G>(q);
             const float tk = P.b[k] - 0.5f * q;
             if (tk > m) {
@@ -281,7 +279,7 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
             const float wk = expf(tk - m);
             s += wk;
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, (c0 + e < d) ? y[e] - pm[e] : 0.f, acc[e]);
+            for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, y[e] - pm[e], acc[e]);
             if (dmu_w) dmu_w[k] = tk;
         }
         const float inv = 1.f / s;
@@ -372,6 +370,11 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
     const RunDesc D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done) return;
+    // phase | 4: run only if the single-pass form of this iteration overflowed its records
+    if (phase & 4) {
+        if (!S->rec_overflow) return;
+        phase &= 3;
+    }
     const ParView P = load_params(C, D, smem, prec_in_smem);
     float *rbase = smem + param_smem_floats(D, prec_in_smem);
     __syncthreads();
@@ -393,7 +396,9 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
     const float dlt = D.delta_p;
     const float keep = D.keep;
 
-    float x[E], p[E], xr[E], g[E], eps[E];
+    float x[E], p[E], xr[E], g[E], eps[E], vmask[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) vmask[e] = (c0 + e < D.d) ? 1.f : 0.f;  // padded components keep p = 0
     int w = 0, t = 0, nref = 0, consec = 0, count = 0, nin = 0, nout = 0;
     float res_ll = 0.f;
     bool active = false, exhausted = false;
@@ -509,12 +514,9 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         float nb[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
+            // padded components stay at 0 inside lo = hi = 0
             const int c = c0 + e;
-            nb[e] = 0.f;
-            if (c < D.d) {
-                if (x[e] < P.lo[c]) nb[e] = -1.f;
-                else if (x[e] > P.hi[c]) nb[e] = 1.f;
-            }
+            nb[e] = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
             outbox += (nb[e] != 0.f);
         }
         outbox = gsum_i<G>(outbox);
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         if (stepping) {
             if (D.noise_mode == 1) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = (c0 + e < D.d) ? fmaf(keep, p[e], dlt * eps[e]) : 0.f;
+                for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * vmask[e]);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
@@ -582,6 +584,284 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
             consec = 0;
         }
         if (stepping) t = ts;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Single-pass HSS (Algorithm 5) when every walker of the launch is resident.
+// A walker steps, records each step (inside flag, reservoir word, log L and, for
+// inside states, x), and registers with run-wide counters the step at which its
+// own n_ref first reaches min_ref and the step at which it meets its stop rule
+// (n_ref >= max_ref and t >= min_steps, or n_steps).  t_save and t_stop are the
+// maxima of those steps, i.e. the first steps at which min over walkers of n_ref
+// reaches min_ref and max_ref.  A walker stops once every walker has registered
+// and it has reached t_stop; steps it took beyond t_stop are discarded.  Because
+// a trajectory depends only on (seed, run, iteration, slot, step), the result
+// equals the three-phase form exactly.  k_hss_pick then replays the reservoir
+// over the recorded window [t_save, t_stop].  A walker that reaches the record
+// length before the run's stop is known sets rec_overflow; the three-phase
+// kernels then redo the iteration.
+// Records of walker w: meta[(w * rec_len + t - 1)] = (word, flags), ll[...] = log L,
+// x[(w * rec_len + t - 1) * xs + c] (inside steps only), rows offset by the run's rec_base.
+// ------------------------------------------------------------------------
+struct RecView {
+    uint2 *meta;
+    float *ll;
+    float *x;
+    int rec_len;  // records per walker
+    int xs;       // floats per x record (the largest d_pad of the batch)
+};
+
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_list, RecView R, const long *rec_base,
+                                                      int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const int r = run_list[blockIdx.y];
+    const RunDesc D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done) return;
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    __syncthreads();
+    const long rb = rec_base[r];  // first record row of this run
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int gbase = lane - lig;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    float *rbuf = rbase + (long)grp * D.d_pad;
+    const int W = D.k;
+    const int dp = D.d_pad;
+    const int L = min(R.rec_len, D.n_steps);
+    const uint32_t iter = static_cast<uint32_t>(S->iter);
+    const float dt = static_cast<float>(S->dt);
+    const float lstar = static_cast<float>(S->lstar);
+    const float dlt = D.delta_p;
+    const float keep = D.keep;
+    volatile int *v_remain = &S->remain_max;
+    volatile int *v_tstop = &S->t_stop1;
+
+    float x[E], p[E], g[E], eps[E], vmask[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) vmask[e] = (c0 + e < D.d) ? 1.f : 0.f;
+    int w = 0, t = 0, nref = 0, consec = 0;
+    bool reg_min = false, reg_max = false;
+    bool active = false, exhausted = false;
+
+    for (;;) {
+        if (!active && !exhausted) {
+            unsigned wid = 0;
+            if (lig == 0) wid = atomicAdd(&S->wcount1, 1u);
+            wid = __shfl_sync(gmask, wid, gbase);
+            if (wid >= static_cast<unsigned>(W)) {
+                exhausted = true;
+            } else {
+                w = static_cast<int>(wid);
+                active = true;
+                const int s0 = C.start_slot[D.w_off + w];
+                const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) x[e] = src[e];
+                lane_normals<E>(D, iter, P_MOM, w, 0, c0, p);
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] *= vmask[e];
+                t = nref = consec = 0;
+                reg_min = reg_max = false;
+                // archive the dead point that this walker's output will replace
+                const int ks = C.order[D.pt_off + w];
+                const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
+                float *ddst = D.dead_x + (D.dead_off + S->n_dead - W + w) * dp + c0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) ddst[e] = ksrc[e];
+                // a rule already met before the first step registers at t = 0
+                reg_min = (D.min_ref == 0);
+                reg_max = (D.max_ref == 0 && D.min_steps <= 0);
+                if (lig == 0) {
+                    if (reg_min) atomicSub(&S->remain_min, 1);
+                    if (reg_max) {
+                        __threadfence();
+                        atomicSub(&S->remain_max, 1);
+                    }
+                }
+            }
+        }
+        if (active) {
+            // stop once every walker has met its stop rule and this one has reached t_stop,
+            // or at the record length / step cap
+            int stop = 0;
+            if (lig == 0) {
+                if (t >= L) {
+                    stop = 1;
+                } else if (reg_max && *v_remain == 0) {
+                    __threadfence();
+                    stop = (t >= *v_tstop);
+                }
+            }
+            stop = __shfl_sync(gmask, stop, gbase);
+            if (stop) {
+                if (lig == 0 && t >= L && !(reg_max && *v_remain == 0 && t >= *v_tstop) && L < D.n_steps)
+                    S->rec_overflow = 1;
+                active = false;
+            }
+        }
+        __syncwarp();
+        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        const bool stepping = active;
+
+        // ---- one step of Algorithm 5 (as in k_hss)
+        const int ts = t + 1;
+        uint32_t spare = 0;
+        lane_normals<E>(D, iter, P_NOISE, w, ts, c0, eps, &spare);
+        const uint32_t res_word = __shfl_sync(0xffffffffu, spare, gbase);
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
+        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        int outbox = 0;
+        float nb[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            nb[e] = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
+            outbox += (nb[e] != 0.f);
+        }
+        outbox = gsum_i<G>(outbox);
+        const bool outside = (outbox > 0) || !(ll > lstar);
+        float pnb = 0.f, pg = 0.f, gg = 0.f;
+        if (__any_sync(0xffffffffu, stepping && outside)) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                pnb = fmaf(p[e], nb[e], pnb);
+                pg = fmaf(p[e], g[e], pg);
+                gg = fmaf(g[e], g[e], gg);
+            }
+            pnb = gsum<G>(pnb);
+            pg = gsum<G>(pg);
+            gg = gsum<G>(gg);
+        }
+        if (stepping && outside) {
+            if (outbox > 0) {
+                const float cc = 2.f * pnb / static_cast<float>(outbox);
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = fmaf(-cc, nb[e], p[e]);
+            } else if (gg > 0.f && gg <= 3.0e38f) {
+                const float cc = 2.f * pg / gg;
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = fmaf(-cc, g[e], p[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = -p[e];
+            }
+        }
+        if (stepping) {
+            if (D.noise_mode == 1) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * vmask[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
+            }
+            nref += outside ? 1 : 0;
+            consec = outside ? consec + 1 : 0;
+            // record the step
+            const long row = rb + (long)w * R.rec_len + (ts - 1);
+            if (!outside) {
+                float *dst = R.x + row * R.xs + c0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) dst[e] = x[e];
+            }
+            if (lig == 0) {
+                R.meta[row] = make_uint2(res_word, outside ? 1u : 0u);
+                R.ll[row] = ll;
+                if (!reg_min && (nref >= D.min_ref || ts >= D.n_steps)) {
+                    atomicMax(&S->t_save1, (nref >= D.min_ref) ? ts : D.n_steps + 1);
+                    __threadfence();
+                    atomicSub(&S->remain_min, 1);
+                }
+                if (!reg_max && ((nref >= D.max_ref && ts >= D.min_steps) || ts >= D.n_steps)) {
+                    atomicMax(&S->t_stop1, ts);
+                    __threadfence();
+                    atomicSub(&S->remain_max, 1);
+                }
+            }
+            reg_min = reg_min || nref >= D.min_ref || ts >= D.n_steps;
+            reg_max = reg_max || (nref >= D.max_ref && ts >= D.min_steps) || ts >= D.n_steps;
+            // pruning: back to the start point with a fresh momentum
+            if (D.prune_after > 0 && consec >= D.prune_after) {
+                const int s0 = C.start_slot[D.w_off + w];
+                const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) x[e] = src[e];
+                lane_normals<E>(D, iter, P_PRUNE, w, ts, c0, p);
+#pragma unroll
+                for (int e = 0; e < E; ++e) p[e] *= vmask[e];
+                consec = 0;
+            }
+            t = ts;
+        }
+    }
+}
+
+// Reservoir replay over the recorded window and emission of every walker's new point.
+template <int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_hss_pick(DevCtx C, const int *run_list, RecView R, const long *rec_base)
+{
+    const int r = run_list[blockIdx.y];
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done || S->rec_overflow) return;
+    const int lane = threadIdx.x & 31, lig = lane % G, gbase = lane - lig;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+    const int grp = (blockIdx.x * HSS_THREADS + threadIdx.x) / G;
+    const int W = D.k, dp = D.d_pad, c0 = lig * E;
+    if (grp >= W) return;
+    const int w = grp;
+    const long base = rec_base[r] + (long)w * R.rec_len;
+    const int ts0 = max(S->t_save1, 1), tstop = S->t_stop1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the tail and the counters read the window of the three-phase form
+        S->t_save = S->t_save1;
+        S->t_stop = S->t_stop1;
+    }
+    int pick = -1, nin = 0, nout = 0;
+    if (lig == 0) {
+        int count = 0;
+        for (int t = 1; t <= tstop; ++t) {
+            const uint2 m = R.meta[base + t - 1];
+            if (m.y) {
+                ++nout;
+            } else {
+                ++nin;
+                if (t >= ts0) {
+                    ++count;
+                    if (((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(count)) >> 32) == 0) pick = t;
+                }
+            }
+        }
+    }
+    pick = __shfl_sync(gmask, pick, gbase);
+    const int slot = C.order[D.pt_off + w];
+    float *dst = C.fa + D.x_off + (long)slot * dp + c0;
+    float out_ll;
+    if (pick > 0) {
+        const float *src = R.x + (base + pick - 1) * R.xs + c0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) dst[e] = src[e];
+        out_ll = R.ll[base + pick - 1];
+    } else {
+        const int s0 = C.start_slot[D.w_off + w];
+        const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) dst[e] = src[e];
+        out_ll = C.logl[D.pt_off + s0];
+    }
+    if (lig == 0) {
+        C.logl[D.pt_off + slot] = out_ll;
+        C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(nin));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
+        if (pick <= 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
     }
 }
 

@@ -47,6 +47,29 @@ static cudaError_t grad_t(const DevCtx &C, int run, double logz, double *part, i
     return cudaGetLastError();
 }
 template <int G, int E>
+static cudaError_t hss1_t(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
+                          size_t smem, int pis, cudaStream_t s)
+{
+    const int gpc = HSS_THREADS / G;
+    const int bx = (max_k + gpc - 1) / gpc;
+    k_hss1<KIND, G, E><<<dim3(bx, nr), HSS_THREADS, smem, s>>>(C, runs, R, rec_base, pis);
+    return cudaGetLastError();
+}
+template <int G, int E>
+static cudaError_t pick_t(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
+                          cudaStream_t s)
+{
+    const int gpc = HSS_THREADS / G;
+    const int bx = (max_k + gpc - 1) / gpc;
+    k_hss_pick<G, E><<<dim3(bx, nr), HSS_THREADS, 0, s>>>(C, runs, R, rec_base);
+    return cudaGetLastError();
+}
+template <int G, int E>
+static cudaError_t occ_t(size_t smem, int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, G, E>, HSS_THREADS, smem);
+}
+template <int G, int E>
 static cudaError_t smem_t(size_t smem)
 {
     if (smem <= 48 * 1024) return cudaSuccess;
@@ -54,6 +77,7 @@ static cudaError_t smem_t(size_t smem)
     cudaError_t e;
     if ((e = cudaFuncSetAttribute((const void *)k_prior_init<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute((const void *)k_hss<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute((const void *)k_hss1<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute((const void *)k_lik_points<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void *)k_grad_means<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
 }
@@ -101,6 +125,20 @@ static cudaError_t grad(int tile, const DevCtx &C, int run, double logz, double 
 static cudaError_t smem_attr(int tile, size_t smem)
 {
     GGNS_DISPATCH(smem_t, smem)
+}
+static cudaError_t hss1(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                        const long *rec_base, size_t smem, int pis, cudaStream_t s)
+{
+    GGNS_DISPATCH(hss1_t, C, runs, nr, max_k, R, rec_base, smem, pis, s)
+}
+static cudaError_t pick(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                        const long *rec_base, cudaStream_t s)
+{
+    GGNS_DISPATCH(pick_t, C, runs, nr, max_k, R, rec_base, s)
+}
+static cudaError_t hss1_occ(int tile, size_t smem, int *blocks_per_sm)
+{
+    GGNS_DISPATCH(occ_t, smem, blocks_per_sm)
 }
 
 }  // namespace GGNS_KIND_NS

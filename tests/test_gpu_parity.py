@@ -271,3 +271,68 @@ def test_rerun_is_deterministic():
     _, ra = _run_gpu([w])
     _, rb = _run_gpu([w])
     assert ra[0]["logz"] == rb[0]["logz"] and ra[0]["n_like"] == rb[0]["n_like"]
+
+
+# ---------------------------------------------------------------- single-pass vs three-phase HSS
+def _hss_outputs(w, x0, l0, lstar, n, monkeypatch, mode, rec_len=None):
+    monkeypatch.setenv("GGNS_HSS", str(mode))
+    if rec_len is None:
+        monkeypatch.delenv("GGNS_REC_LEN", raising=False)
+    else:
+        monkeypatch.setenv("GGNS_REC_LEN", str(rec_len))
+    s = ggns.Sampler([w])
+    xo = torch.zeros((n, x0.shape[1]), device="cuda")
+    lo_ = torch.zeros(n, device="cuda")
+    x0d, l0d = _dev(x0, torch.float32), _dev(l0, torch.float32)
+    st = s.hss(x0d.data_ptr(), l0d.data_ptr(), n, lstar, 0.01, 3, xo.data_ptr(), lo_.data_ptr())
+    return st, xo.cpu().numpy(), lo_.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,d,n", [("iso", 8, 16), ("mix", 32, 500), ("dense", 16, 64), ("rosen", 6, 33)])
+def test_single_pass_hss_equals_three_phases(kind, d, n, monkeypatch):
+    """Algorithm 5 in one pass with step records and a replayed reservoir gives the
+    three-phase result bit for bit, also when the records overflow (record length 3)
+    and the iteration is redone in three phases."""
+    w = W.small_workload(kind, d, 2 * n, seed=21)
+    w = dict(w, cfg=dict(w["cfg"], n_steps=200))
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(8)
+    center = np.zeros(d) if kind != "mix" else w["spec"]["means"][0]
+    if kind == "rosen":
+        center = np.full(d, 0.3)
+    x0 = (center + _ball_start(d, n, 0.15, rng)).astype(np.float32).astype(np.float64)
+    l0 = np.array([lik.loglik(v) for v in x0])
+    lstar = float(np.float32(np.min(l0) - 0.01 * abs(np.min(l0)) - 0.5))
+    ref = _hss_outputs(w, x0, l0, lstar, n, monkeypatch, 3)
+    for rec_len in (None, 3):
+        got = _hss_outputs(w, x0, l0, lstar, n, monkeypatch, 0, rec_len)
+        assert got[0] == ref[0]
+        np.testing.assert_array_equal(got[1], ref[1])
+        np.testing.assert_array_equal(got[2], ref[2])
+
+
+def test_single_pass_runs_equal_three_phase_runs(monkeypatch):
+    """Whole clustered runs: the single-pass HSS (with and without record overflows)
+    reproduces the three-phase runs exactly."""
+    ws = [W.small_workload("mix", 8, 300, seed=23, clustering=1), W.small_workload("iso", 5, 120, seed=24)]
+    out = {}
+    for mode, rec_len in ((3, None), (0, None), (0, 4)):
+        monkeypatch.setenv("GGNS_HSS", str(mode))
+        if rec_len is None:
+            monkeypatch.delenv("GGNS_REC_LEN", raising=False)
+        else:
+            monkeypatch.setenv("GGNS_REC_LEN", str(rec_len))
+        s, res = _run_gpu(ws)
+        prof = s.profile()
+        out[(mode, rec_len)] = (res, [s.samples(r) for r in range(len(ws))], prof)
+    ref_res, ref_smp, ref_prof = out[(3, None)]
+    assert ref_prof["rec_len"] == 0
+    assert out[(0, None)][2]["rec_len"] > 0
+    assert out[(0, 4)][2]["rec_overflows"] > 0
+    for key in ((0, None), (0, 4)):
+        res, smp, _ = out[key]
+        for a, b in zip(res, ref_res):
+            assert a == b
+        for (xa, la), (xb, lb) in zip(smp, ref_smp):
+            np.testing.assert_array_equal(xa, xb)
+            np.testing.assert_array_equal(la, lb)
