@@ -10,7 +10,7 @@
 namespace ggns {
 
 constexpr int CMAX = 64;        // cluster slots per run
-constexpr int KNN_K = 16;       // neighbour ranks precomputed per point for Algorithm 4
+constexpr int KNN_K = 16;       // neighbour ranks precomputed per point for Algorithm 4 (later ranks: exact scan)
 constexpr int NLIVE_MAX = 16384;
 constexpr int KMAX_COMP = 64;   // mixture components
 constexpr int DMAX = 512;

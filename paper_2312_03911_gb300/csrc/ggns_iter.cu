@@ -817,19 +817,30 @@ __global__ void k_tail(DevCtx C, int r0)
 // lists are merged through shared memory at the end.
 constexpr int KQ_WARPS = 4;
 
-__device__ __forceinline__ void knn_insert(unsigned long long (&L)[KNN_K], unsigned long long key)
+// Insert candidate j with squared-distance bits dk into the ascending list
+// (D, I).  Candidates arrive in ascending j, so keeping an equal distance ahead
+// of the newcomer orders the list by (distance, index).  Every position is
+// updated from the old list at once (no chain of swaps).
+__device__ __forceinline__ void knn_push(uint32_t (&D)[KNN_K], int (&I)[KNN_K], uint32_t dk, int j)
 {
-    if (key < L[KNN_K - 1]) {
-        L[KNN_K - 1] = key;
+    if (dk < D[KNN_K - 1]) {
 #pragma unroll
         for (int q = KNN_K - 1; q > 0; --q) {
-            if (L[q] < L[q - 1]) {
-                const unsigned long long tmp = L[q];
-                L[q] = L[q - 1];
-                L[q - 1] = tmp;
-            }
+            const bool shift = D[q - 1] > dk;
+            const bool here = D[q] > dk;
+            D[q] = shift ? D[q - 1] : (here ? dk : D[q]);
+            I[q] = shift ? I[q - 1] : (here ? j : I[q]);
+        }
+        if (D[0] > dk) {
+            D[0] = dk;
+            I[0] = j;
         }
     }
+}
+
+__device__ __forceinline__ unsigned long long knn_key(uint32_t dk, int j)
+{
+    return (j < 0) ? ~0ull : (((unsigned long long)dk << 32) | (unsigned)j);
 }
 
 // Squared distance in coordinate order: each squared difference is added with
@@ -844,39 +855,116 @@ __device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d
     return s;
 }
 
+// Queries of one CTA, grouped by label.  The n points are ordered by (label,
+// index); CTA b takes positions [32 b, 32 b + 32) of that order, so its queries
+// come from one or two clusters and it scans only candidates with those labels.
+// q_slot[32] receives the query indices (-1 past n); returns the label set as a
+// bit mask.  Every CTA computes the label counts itself (n reads).
+__device__ unsigned long long knn_block_queries(int n, const int *label, int *q_slot, int *s_cnt /* [CMAX] */,
+                                                int *s_wsum /* [KQ_WARPS] */)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < CMAX) s_cnt[tid] = 0;
+    if (tid < 32) q_slot[tid] = -1;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&s_cnt[label[i]], 1);
+    __syncthreads();
+    const int p0 = blockIdx.x * 32, p1 = min(p0 + 32, n);
+    unsigned long long mask = 0;
+    int off = 0;
+    for (int c = 0; c < CMAX; ++c) {
+        const int cnt = s_cnt[c];
+        const int lo = max(p0, off), hi = min(p1, off + cnt);
+        if (lo < hi) {
+            mask |= 1ull << c;
+            // ranks [lo - off, hi - off) of label c, by ascending index
+            const int r0 = lo - off, r1 = hi - off;
+            int base = 0;
+            for (int i0 = 0; i0 < n && base < r1; i0 += blockDim.x) {
+                const int i = i0 + tid;
+                const bool f = (i < n) && label[i] == c;
+                const unsigned bal = __ballot_sync(0xffffffffu, f);
+                if (lane == 0) s_wsum[warp] = __popc(bal);
+                __syncthreads();
+                int before = base;
+                for (int w2 = 0; w2 < warp; ++w2) before += s_wsum[w2];
+                if (f) {
+                    const int rk = before + __popc(bal & ((1u << lane) - 1u));
+                    if (rk >= r0 && rk < r1) q_slot[off + rk - p0] = i;
+                }
+                int tot = 0;
+                for (int w2 = 0; w2 < KQ_WARPS; ++w2) tot += s_wsum[w2];
+                __syncthreads();
+                base += tot;
+            }
+        }
+        off += cnt;
+    }
+    __syncthreads();
+    return mask;
+}
+
 // QR: query components held in registers (d <= QR, QR a multiple of 4).  The
-// candidates stream through shared memory in tiles of KQ_TILE rows (coalesced
-// loads by the whole CTA); every lane of a warp then reads the same row (a
-// broadcast), two candidates at a time for independent accumulation chains.
+// candidates whose label is one of the CTA's stream through shared memory in
+// tiles (compacted, ascending index, coalesced loads by the whole CTA); every
+// lane of a warp then reads the same row (a broadcast), two candidates at a
+// time for independent accumulation chains.
 constexpr int KQ_TILE = 128;
+static_assert(KQ_TILE == KQ_WARPS * 32, "one tile row per thread in the compaction");
+constexpr int KQ_MSTRIDE = KNN_K + 1;  // merge-list stride per lane (u64): spreads the banks
 
 template <int QR>
 __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
-                          unsigned long long *merge /* [KQ_WARPS][32][KNN_K] */, float *tile /* [KQ_TILE][QR] */,
-                          int *tlab /* [KQ_TILE] */)
+                          unsigned long long *merge /* [KQ_WARPS][32][KQ_MSTRIDE] */,
+                          float *tile /* [KQ_TILE][QR] */, int *tidx /* [KQ_TILE] */, int *tlab /* [KQ_TILE] */,
+                          int *q_slot /* [32] */, int *s_cnt /* [CMAX] */, int *s_wsum /* [KQ_WARPS] */)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 32 + lane;
-    const bool act = i < n;
+    const unsigned long long lmask = knn_block_queries(n, label, q_slot, s_cnt, s_wsum);
+    const int i = q_slot[lane];
+    const bool act = i >= 0;
     const int li = act ? label[i] : -1;
     const bool need = act && csize[li] >= 3;
     const bool any_need = __syncthreads_or(need);
     float q[QR];
 #pragma unroll
     for (int t = 0; t < QR; ++t) q[t] = (act && t < d) ? x[(long)i * xstride + t] : 0.f;
-    unsigned long long L[KNN_K];
+    uint32_t Dl[KNN_K];
+    int Il[KNN_K];
 #pragma unroll
-    for (int u = 0; u < KNN_K; ++u) L[u] = ~0ull;
+    for (int u = 0; u < KNN_K; ++u) {
+        Dl[u] = 0xffffffffu;
+        Il[u] = -1;
+    }
     if (any_need) {
         for (int j0 = 0; j0 < n; j0 += KQ_TILE) {
+            // compact the candidates of this tile whose label belongs to the CTA
+            const int jj = j0 + threadIdx.x;  // KQ_TILE == blockDim.x
+            const int lj = (jj < n) ? label[jj] : -1;
+            const bool f = lj >= 0 && ((lmask >> lj) & 1ull);
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            __syncthreads();  // the previous tile is no longer read
+            if (lane == 0) s_wsum[warp] = __popc(bal);
             __syncthreads();
-            // rows padded with zeros up to QR (the query is zero there too)
-            for (int e = threadIdx.x; e < KQ_TILE * (QR / 4); e += blockDim.x) {
+            int pos = __popc(bal & ((1u << lane) - 1u)), rows = 0;
+            for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
+                pos += (w2 < warp) ? s_wsum[w2] : 0;
+                rows += s_wsum[w2];
+            }
+            if (f) {
+                tidx[pos] = jj;
+                tlab[pos] = lj;
+            }
+            if (rows == 0) continue;
+            __syncthreads();
+            // rows padded with zeros up to QR (the query is zero there too); one row past
+            // the last keeps the pair loop inside the tile
+            const int rows2 = min(rows + 1, KQ_TILE);
+            for (int e = threadIdx.x; e < rows2 * (QR / 4); e += blockDim.x) {
                 const int rr = e / (QR / 4), t4 = (e - rr * (QR / 4)) * 4;
-                const int j = j0 + rr;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < n) {
-                    const float *row = x + (long)j * xstride;
+                if (rr < rows) {
+                    const float *row = x + (long)tidx[rr] * xstride;
                     if (t4 + 0 < d) v.x = row[t4 + 0];
                     if (t4 + 1 < d) v.y = row[t4 + 1];
                     if (t4 + 2 < d) v.z = row[t4 + 2];
@@ -884,12 +972,10 @@ __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *
                 }
                 *reinterpret_cast<float4 *>(tile + rr * QR + t4) = v;
             }
-            for (int rr = threadIdx.x; rr < KQ_TILE; rr += blockDim.x) tlab[rr] = (j0 + rr < n) ? label[j0 + rr] : -1;
             __syncthreads();
-            const int rows = min(KQ_TILE, n - j0);
             for (int rr = warp * 2; rr < rows; rr += 2 * KQ_WARPS) {
                 const float *ra = tile + rr * QR;
-                const float *rb = tile + (rr + 1) * QR;  // inside the tile (zeros past n)
+                const float *rb = tile + (rr + 1) * QR;  // inside the tile (zeros past the rows)
                 float sa = 0.f, sb = 0.f;
 #pragma unroll
                 for (int t = 0; t < QR; t += 4) {
@@ -911,15 +997,17 @@ __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *
                     sa = __fmaf_rn(da, da, sa);
                     sb = __fmaf_rn(db, db, sb);
                 }
-                const int ja = j0 + rr, jb = ja + 1;
-                if (need && tlab[rr] == li && ja != i) knn_insert(L, ((unsigned long long)__float_as_uint(sa) << 32) | (unsigned)ja);
-                if (need && rr + 1 < rows && tlab[rr + 1] == li && jb != i)
-                    knn_insert(L, ((unsigned long long)__float_as_uint(sb) << 32) | (unsigned)jb);
+                const int ja = tidx[rr];
+                if (need && tlab[rr] == li && ja != i) knn_push(Dl, Il, __float_as_uint(sa), ja);
+                if (rr + 1 < rows) {
+                    const int jb = tidx[rr + 1];
+                    if (need && tlab[rr + 1] == li && jb != i) knn_push(Dl, Il, __float_as_uint(sb), jb);
+                }
             }
         }
     }
 #pragma unroll
-    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KNN_K + u] = L[u];
+    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KQ_MSTRIDE + u] = knn_key(Dl[u], Il[u]);
     __syncthreads();
     if (warp == 0) {
         // merge the KQ_WARPS sorted lists of this lane's query
@@ -931,7 +1019,8 @@ __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *
             int bw = 0;
 #pragma unroll
             for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
-                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KNN_K + pos[w2]] : ~0ull;
+                const unsigned long long v =
+                    (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KQ_MSTRIDE + pos[w2]] : ~0ull;
                 if (v < best) {
                     best = v;
                     bw = w2;
@@ -955,18 +1044,22 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
     const int li = act ? label[i] : -1;
     const bool need = act && csize[li] >= 3;
     const float *qi = x + (long)(act ? i : 0) * xstride;
-    unsigned long long L[KNN_K];
+    uint32_t Dl[KNN_K];
+    int Il[KNN_K];
 #pragma unroll
-    for (int u = 0; u < KNN_K; ++u) L[u] = ~0ull;
+    for (int u = 0; u < KNN_K; ++u) {
+        Dl[u] = 0xffffffffu;
+        Il[u] = -1;
+    }
     if (__any_sync(0xffffffffu, need)) {
         for (int j = warp; j < n; j += KQ_WARPS) {
             const int lj = label[j];
             const float s = sqdist_rn(qi, x + (long)j * xstride, d);
-            if (need && lj == li && j != i) knn_insert(L, ((unsigned long long)__float_as_uint(s) << 32) | (unsigned)j);
+            if (need && lj == li && j != i) knn_push(Dl, Il, __float_as_uint(s), j);
         }
     }
 #pragma unroll
-    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KNN_K + u] = L[u];
+    for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KQ_MSTRIDE + u] = knn_key(Dl[u], Il[u]);
     __syncthreads();
     if (warp == 0) {
         int pos[KQ_WARPS];
@@ -977,7 +1070,7 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
             int bw = 0;
 #pragma unroll
             for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
-                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KNN_K + pos[w2]] : ~0ull;
+                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KQ_MSTRIDE + pos[w2]] : ~0ull;
                 if (v < best) {
                     best = v;
                     bw = w2;
@@ -991,17 +1084,22 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
     }
 }
 
-// shared memory: merge lists [KQ_WARPS][32][KNN_K] u64 | tile [KQ_TILE][64] f32 | tile labels [KQ_TILE]
+// shared memory: merge lists [KQ_WARPS][32][KQ_MSTRIDE] u64 | tile [KQ_TILE][64] f32 | tile indices and
+// labels [KQ_TILE] | query slots [32] | label counts [CMAX] | warp sums [KQ_WARPS]
 __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
                          float *smem)
 {
     unsigned long long *merge = reinterpret_cast<unsigned long long *>(smem);
-    float *tile = reinterpret_cast<float *>(merge + KQ_WARPS * 32 * KNN_K);
-    int *tlab = reinterpret_cast<int *>(tile + KQ_TILE * 64);
-    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
-    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
-    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
-    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, csize, nbr, merge, tile, tlab);
+    float *tile = reinterpret_cast<float *>(merge + KQ_WARPS * 32 * KQ_MSTRIDE);
+    int *tidx = reinterpret_cast<int *>(tile + KQ_TILE * 64);
+    int *tlab = tidx + KQ_TILE;
+    int *q_slot = tlab + KQ_TILE;
+    int *s_cnt = q_slot + 32;
+    int *s_wsum = s_cnt + CMAX;
+    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
+    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
+    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
+    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
     else knn_lanes_wide(x, xstride, n, d, label, csize, nbr, merge);
 }
 
@@ -1018,8 +1116,8 @@ __global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
 size_t knn_smem_bytes(int d)
 {
     (void)d;
-    return sizeof(unsigned long long) * (size_t)KQ_WARPS * 32 * KNN_K + sizeof(float) * KQ_TILE * 64 +
-           sizeof(int) * KQ_TILE;
+    return sizeof(unsigned long long) * (size_t)KQ_WARPS * 32 * KQ_MSTRIDE + sizeof(float) * KQ_TILE * 64 +
+           sizeof(int) * (2 * KQ_TILE + 32 + CMAX + KQ_WARPS);
 }
 
 // Union-find in shared memory: roots are the smallest member index.

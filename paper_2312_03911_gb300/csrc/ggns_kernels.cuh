@@ -613,8 +613,8 @@ struct RecView {
 };
 
 template <int KIND, int G, int E>
-__global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_list, RecView R, const long *rec_base,
-                                                      int prec_in_smem)
+__global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx C, const int *run_list, RecView R,
+                                                                         const long *rec_base, int prec_in_smem)
 {
     extern __shared__ float smem[];
     const int r = run_list[blockIdx.y];
@@ -649,6 +649,12 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_l
     int w = 0, t = 0, nref = 0, consec = 0;
     bool reg_min = false, reg_max = false;
     bool active = false, exhausted = false;
+    // lane 0 of a group: walkers still to register (read one step ahead) and, once
+    // that reached 0, the final t_stop
+    int rem_seen = 1, tstop_final = -1;
+    // noise of the next step (it depends only on slot and step, so it is drawn a
+    // step ahead, beside the current step's likelihood)
+    uint32_t spare = 0;
 
     for (;;) {
         if (!active && !exhausted) {
@@ -667,8 +673,10 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_l
                 lane_normals<E>(D, iter, P_MOM, w, 0, c0, p);
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] *= vmask[e];
+                lane_normals<E>(D, iter, P_NOISE, w, 1, c0, eps, &spare);
                 t = nref = consec = 0;
-                reg_min = reg_max = false;
+                rem_seen = 1;
+                tstop_final = -1;
                 // archive the dead point that this walker's output will replace
                 const int ks = C.order[D.pt_off + w];
                 const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
@@ -692,29 +700,39 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_l
             // or at the record length / step cap
             int stop = 0;
             if (lig == 0) {
+                if (reg_max && rem_seen == 0 && tstop_final < 0) {
+                    // every walker has registered: t_stop is final (read after the count)
+                    __threadfence();
+                    tstop_final = *v_tstop;
+                }
                 if (t >= L) {
                     stop = 1;
-                } else if (reg_max && *v_remain == 0) {
-                    __threadfence();
-                    stop = (t >= *v_tstop);
+                    if (!(tstop_final >= 0 && t >= tstop_final) && L < D.n_steps) {
+                        // the stop may not be known yet: decide on fresh values
+                        const int rem_now = *v_remain;
+                        __threadfence();
+                        if (!(reg_max && rem_now == 0 && t >= *v_tstop)) S->rec_overflow = 1;
+                    }
+                } else if (tstop_final >= 0 && t >= tstop_final) {
+                    stop = 1;
                 }
             }
             stop = __shfl_sync(gmask, stop, gbase);
-            if (stop) {
-                if (lig == 0 && t >= L && !(reg_max && *v_remain == 0 && t >= *v_tstop) && L < D.n_steps)
-                    S->rec_overflow = 1;
-                active = false;
-            }
+            if (stop) active = false;
         }
         __syncwarp();
         if (!__any_sync(0xffffffffu, active || !exhausted)) break;
         const bool stepping = active;
+        // the registration count for the next stop test, read while this step runs
+        if (lig == 0 && stepping && reg_max && rem_seen != 0) rem_seen = *v_remain;
 
         // ---- one step of Algorithm 5 (as in k_hss)
         const int ts = t + 1;
-        uint32_t spare = 0;
-        lane_normals<E>(D, iter, P_NOISE, w, ts, c0, eps, &spare);
         const uint32_t res_word = __shfl_sync(0xffffffffu, spare, gbase);
+        float ecur[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) ecur[e] = eps[e];
+        lane_normals<E>(D, iter, P_NOISE, w, ts + 1, c0, eps, &spare);
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
@@ -757,10 +775,10 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss1(DevCtx C, const int *run_l
         if (stepping) {
             if (D.noise_mode == 1) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * vmask[e]);
+                for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * ecur[e] * vmask[e]);
             } else {
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
+                for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, ecur[e], 1.f);
             }
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;

@@ -76,6 +76,20 @@ def test_knn_components_bit_exact(seed, m, d, k):
     np.testing.assert_array_equal(comp.cpu().numpy(), comp_ref)
 
 
+@pytest.mark.parametrize("seed", [596, 773])
+def test_knn_components_beyond_precomputed_ranks(seed):
+    """A chain with heavy-tailed gaps keeps merging up to rank 10 of Algorithm 4, past the
+    ranks the k-NN kernel precomputes, so the exact scan for later ranks is exercised."""
+    rng = np.random.default_rng(seed)
+    x = np.cumsum(rng.exponential(1.0, (60, 2)) ** 3, axis=0).astype(np.float32)
+    xd = _dev(x, torch.float32)
+    comp = torch.zeros(len(x), dtype=torch.int32, device="cuda")
+    nc = ggns.knn_components(xd.data_ptr(), len(x), 2, comp.data_ptr())
+    n_ref, comp_ref = oracle.knn_components(x)
+    assert nc == n_ref
+    np.testing.assert_array_equal(comp.cpu().numpy(), comp_ref)
+
+
 def test_knn_components_lattice_ties():
     g = np.array([[i, j] for i in range(6) for j in range(6)], np.float32)
     x = np.concatenate([g, g + 20.0, g * 0.5 - 30.0]).astype(np.float32)
