@@ -59,7 +59,8 @@ struct RunClass {
     int max_k = 0, max_n = 0;
     size_t smem = 0;
     int prec_in_smem = 0;
-    int single = 0;  // HSS in one pass (every walker block resident at once)
+    int single = 0;    // HSS in one pass (every walker block resident at once)
+    int fallback = 1;  // three-phase kernels after the single pass (records shorter than n_steps)
 };
 
 // Runs advanced together by one CUDA graph on one stream.  Different groups
@@ -370,12 +371,12 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
         }
     for (auto &cl : g.classes)
         if (cl.single) {
-            CU(kind_launch(cl.kind).pick(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
-                                         ctx->rec_base_dev, s));
+            CU(launch_hss_pick(C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec, ctx->rec_base_dev, s));
             ++n;
         }
     for (int phase = 0; phase < 3; ++phase)
         for (auto &cl : g.classes) {
+            if (cl.single && !cl.fallback) continue;  // records cover n_steps: no overflow
             CU(kind_launch(cl.kind).hss(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k,
                                         cl.single ? (phase | 4) : phase, cl.smem, cl.prec_in_smem, s));
             ++n;
@@ -660,7 +661,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         CK(setup_cls());
     }
     // single-pass HSS records: GGNS_HSS = 3 keeps the three-phase form, GGNS_REC_LEN
-    // sets the records per walker (default 256, bounded by n_steps and a 4 GiB budget)
+    // sets the records per walker (default n_steps, halved until they fit 8 GiB)
     int n_sm = 0;
     auto smq = [&]() -> ns_status {
         CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -669,7 +670,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
     CK(smq());
     {
         if (const char *v = getenv("GGNS_HSS")) ctx->hss_mode = atoi(v);
-        long rec_len = 256;
+        long rec_len = 1l << 30;
         if (const char *v = getenv("GGNS_REC_LEN")) rec_len = std::max(1, atoi(v));
         int max_steps = 0, xs = 0;
         long walkers = 0;
@@ -679,7 +680,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
             walkers += ctx->desc[r].k;
         }
         rec_len = std::min<long>(rec_len, max_steps);
-        const long budget = 4l << 30;
+        const long budget = 8l << 30;
         const long row_bytes = (long)xs * 4 + 12;
         while (rec_len > 16 && walkers * rec_len * row_bytes > budget) rec_len /= 2;
         if (ctx->hss_mode != 3 && walkers * rec_len * row_bytes <= budget) {
@@ -742,6 +743,8 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                         const long gpc = HSS_THREADS / tile_of(rc.tile).g;
                         const long blocks = (rc.max_k + gpc - 1) / gpc * (long)rc.runs.size();
                         rc.single = blocks <= (long)per_sm * n_sm ? 1 : 0;
+                        rc.fallback = 0;
+                        for (int r : rc.runs) rc.fallback |= (ctx->rec.rec_len < cfg[r].n_steps);
                     }
                 }
                 CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
@@ -1341,7 +1344,7 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         CU(cudaMalloc(&rbase, sizeof(long)));
         CU(cudaMemcpyAsync(rbase, &zero_base, sizeof(long), cudaMemcpyHostToDevice, s));
         CU(kind_launch(D.kind).hss1(D.tile, C, runs, 1, (int)n, R, rbase, rc.smem, rc.prec_in_smem, s));
-        CU(kind_launch(D.kind).pick(D.tile, C, runs, 1, (int)n, R, rbase, s));
+        CU(launch_hss_pick(C, runs, 1, (int)n, R, rbase, s));
     }
     for (int phase = 0; phase < 3; ++phase)
         CU(kind_launch(D.kind).hss(D.tile, C, runs, 1, (int)n, single ? (phase | 4) : phase, rc.smem,

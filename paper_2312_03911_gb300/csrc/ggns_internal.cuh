@@ -25,6 +25,15 @@ struct Tile {
     int g, e;
 };
 
+// Step records of the single-pass HSS (one row per walker-step).
+struct RecView {
+    uint2 *meta;
+    float *ll;
+    float *x;
+    int rec_len;  // records per walker
+    int xs;       // floats per x record (the largest d_pad of the batch)
+};
+
 // Constant description of one run (device copy, read by every kernel).
 struct RunDesc {
     int d, d_pad, n_live, k, kind, n_comp;

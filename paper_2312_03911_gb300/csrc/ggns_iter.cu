@@ -12,10 +12,65 @@ namespace ggns {
 // ------------------------------------------------------------------------
 // Block-wide bitonic sort of npow2 64-bit keys in shared memory (ascending).
 // ------------------------------------------------------------------------
+// Ascending bitonic sort of npow2 keys in shared memory by the whole block.
+// Stages whose partner distance j is at least 32 exchange through shared memory
+// (one barrier each); the stages with j < 32 of each merge run in registers with
+// warp shuffles: element i = tid + m * blockDim and its partner i ^ j sit in the
+// same warp at the same m.  blockDim is a multiple of 32.
+__device__ __forceinline__ unsigned long long bitonic_shfl_step(unsigned long long v, int i, int j, int k)
+{
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, j);
+    const bool up = (i & k) == 0;     // ascending block of the merge
+    const bool lower = (i & j) == 0;  // this element takes the smaller key when ascending
+    const bool take_min = (up == lower);
+    return take_min ? (o < v ? o : v) : (o > v ? o : v);
+}
+
+__device__ void bitonic_warp_stages(unsigned long long *keys, int npow2, int k, int j_top)
+{
+    // stages j = j_top, j_top / 2, ..., 1 of the merge of size k, in registers
+    for (int i0 = 0; i0 < npow2; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        if (i0 + (int)(threadIdx.x & ~31u) >= npow2) continue;  // whole warp past the keys
+        unsigned long long v = keys[i];
+        for (int j = j_top; j > 0; j >>= 1) v = bitonic_shfl_step(v, i, j, k);
+        keys[i] = v;
+    }
+}
+
 __device__ void block_bitonic_sort(unsigned long long *keys, int npow2)
 {
-    for (int k = 2; k <= npow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
+    if (npow2 < 32) {
+        for (int k = 2; k <= npow2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const unsigned long long a = keys[i], b = keys[ixj];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) {
+                            keys[i] = b;
+                            keys[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        return;
+    }
+    // merges of size 2 .. 32: all stages inside a warp
+    for (int i0 = 0; i0 < npow2; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        if (i0 + (int)(threadIdx.x & ~31u) >= npow2) continue;
+        unsigned long long v = keys[i];
+        for (int k = 2; k <= 32; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) v = bitonic_shfl_step(v, i, j, k);
+        keys[i] = v;
+    }
+    __syncthreads();
+    for (int k = 64; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j >= 32; j >>= 1) {
             for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
@@ -29,6 +84,8 @@ __device__ void block_bitonic_sort(unsigned long long *keys, int npow2)
             }
             __syncthreads();
         }
+        bitonic_warp_stages(keys, npow2, k, 16);
+        __syncthreads();
     }
 }
 
@@ -804,6 +861,61 @@ __global__ void k_tail(DevCtx C, int r0)
     }
 }
 
+// Reservoir replay over the recorded window and emission of every walker's new
+// point, one warp per walker: lane l reads the records of steps 32 m + l + 1, the
+// saved steps of a round are counted with a ballot, and the last step whose
+// acceptance test passes (word * count < 2^32, count = rank among the saved
+// steps) is the pick -- the same sequence of decisions as the sequential reservoir.
+constexpr int PICK_WARPS = 4;
+
+__global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const int *run_list, RecView R,
+                                                              const long *rec_base)
+{
+    const int r = run_list[blockIdx.y];
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done || S->rec_overflow) return;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * PICK_WARPS + (threadIdx.x >> 5);
+    const int W = D.k, dp = D.d_pad;
+    const int ts0 = max(S->t_save1, 1), tstop = S->t_stop1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // the tail and the counters read the window of the three-phase form
+        S->t_save = S->t_save1;
+        S->t_stop = S->t_stop1;
+    }
+    if (w >= W) return;
+    const long base = rec_base[r] + (long)w * R.rec_len;
+    int pick = 0, count = 0, nout = 0;
+    for (int t0 = 1; t0 <= tstop; t0 += 32) {
+        const int t = t0 + lane;
+        uint2 m = make_uint2(0u, 0u);
+        if (t <= tstop) m = R.meta[base + t - 1];
+        const bool in_win = t <= tstop;
+        const bool outside = in_win && m.y != 0u;
+        const bool saved = in_win && !outside && t >= ts0;
+        const unsigned smask = __ballot_sync(0xffffffffu, saved);
+        const int cnt = count + __popc(smask & ((1u << lane) - 1u)) + 1;
+        const bool acc = saved && ((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(cnt)) >> 32) == 0;
+        const unsigned amask = __ballot_sync(0xffffffffu, acc);
+        if (amask) pick = t0 + 31 - __clz(amask);
+        count += __popc(smask);
+        nout += __popc(__ballot_sync(0xffffffffu, outside));
+    }
+    const int slot = C.order[D.pt_off + w];
+    float *dst = C.fa + D.x_off + (long)slot * dp;
+    const float *src = (pick > 0) ? R.x + (base + pick - 1) * R.xs
+                                  : C.fa + D.x_off + (long)C.start_slot[D.w_off + w] * dp;
+    for (int c = lane; c < dp; c += 32) dst[c] = src[c];
+    if (lane == 0) {
+        C.logl[D.pt_off + slot] = (pick > 0) ? R.ll[base + pick - 1] : C.logl[D.pt_off + C.start_slot[D.w_off + w]];
+        C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(tstop - nout));
+        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
+        if (pick <= 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
+    }
+}
+
 // ------------------------------------------------------------------------
 // Cluster finding (Algorithm 4)
 // ------------------------------------------------------------------------
@@ -1540,6 +1652,12 @@ cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cu
 cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
 {
     k_final<<<n_runs, SEL_THREADS, smem, s>>>(C, r0);
+    return cudaGetLastError();
+}
+cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
+                            cudaStream_t s)
+{
+    k_hss_pick<<<dim3((max_k + PICK_WARPS - 1) / PICK_WARPS, nr), PICK_WARPS * 32, 0, s>>>(C, runs, R, rec_base);
     return cudaGetLastError();
 }
 cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s)

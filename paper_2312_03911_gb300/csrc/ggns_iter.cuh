@@ -25,6 +25,8 @@ cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t c
 cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                            const long *rec_base, cudaStream_t s);
 cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
 cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s);
 cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
@@ -45,7 +47,6 @@ cudaError_t launch_stats_plain(Stats *st, double *zz, int k, const double *kL, c
 void set_global_error(const char *msg);
 
 // per likelihood kind (ggns_k_<kind>.cu)
-struct RecView;
 struct KindLaunch {
     cudaError_t (*prior)(int tile, const DevCtx &C, const int *runs, int nr, int max_n, size_t smem, int pis,
                          cudaStream_t s);
@@ -58,8 +59,6 @@ struct KindLaunch {
     cudaError_t (*set_smem)(int tile, size_t smem);
     cudaError_t (*hss1)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                         const long *rec_base, size_t smem, int pis, cudaStream_t s);
-    cudaError_t (*pick)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
-                        const long *rec_base, cudaStream_t s);
     cudaError_t (*hss1_occ)(int tile, size_t smem, int *blocks_per_sm);
 };
 const KindLaunch &kind_launch(int kind);

@@ -7,7 +7,7 @@ namespace ggns {
 const KindLaunch &kind_launch_rosen()
 {
     static const KindLaunch L{kind_rosen::prior, kind_rosen::hss, kind_rosen::lik, kind_rosen::grad, kind_rosen::smem_attr, kind_rosen::hss1,
-                                kind_rosen::pick, kind_rosen::hss1_occ};
+                                kind_rosen::hss1_occ};
     return L;
 }
 }  // namespace ggns

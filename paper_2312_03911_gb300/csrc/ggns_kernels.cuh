@@ -604,13 +604,6 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 // Records of walker w: meta[(w * rec_len + t - 1)] = (word, flags), ll[...] = log L,
 // x[(w * rec_len + t - 1) * xs + c] (inside steps only), rows offset by the run's rec_base.
 // ------------------------------------------------------------------------
-struct RecView {
-    uint2 *meta;
-    float *ll;
-    float *x;
-    int rec_len;  // records per walker
-    int xs;       // floats per x record (the largest d_pad of the batch)
-};
 
 template <int KIND, int G, int E>
 __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx C, const int *run_list, RecView R,
@@ -818,68 +811,6 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
             }
             t = ts;
         }
-    }
-}
-
-// Reservoir replay over the recorded window and emission of every walker's new point.
-template <int G, int E>
-__global__ void __launch_bounds__(HSS_THREADS) k_hss_pick(DevCtx C, const int *run_list, RecView R, const long *rec_base)
-{
-    const int r = run_list[blockIdx.y];
-    const RunDesc &D = C.desc[r];
-    RunState *S = C.state + r;
-    if (S->done || S->rec_overflow) return;
-    const int lane = threadIdx.x & 31, lig = lane % G, gbase = lane - lig;
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
-    const int grp = (blockIdx.x * HSS_THREADS + threadIdx.x) / G;
-    const int W = D.k, dp = D.d_pad, c0 = lig * E;
-    if (grp >= W) return;
-    const int w = grp;
-    const long base = rec_base[r] + (long)w * R.rec_len;
-    const int ts0 = max(S->t_save1, 1), tstop = S->t_stop1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // the tail and the counters read the window of the three-phase form
-        S->t_save = S->t_save1;
-        S->t_stop = S->t_stop1;
-    }
-    int pick = -1, nin = 0, nout = 0;
-    if (lig == 0) {
-        int count = 0;
-        for (int t = 1; t <= tstop; ++t) {
-            const uint2 m = R.meta[base + t - 1];
-            if (m.y) {
-                ++nout;
-            } else {
-                ++nin;
-                if (t >= ts0) {
-                    ++count;
-                    if (((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(count)) >> 32) == 0) pick = t;
-                }
-            }
-        }
-    }
-    pick = __shfl_sync(gmask, pick, gbase);
-    const int slot = C.order[D.pt_off + w];
-    float *dst = C.fa + D.x_off + (long)slot * dp + c0;
-    float out_ll;
-    if (pick > 0) {
-        const float *src = R.x + (base + pick - 1) * R.xs + c0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) dst[e] = src[e];
-        out_ll = R.ll[base + pick - 1];
-    } else {
-        const int s0 = C.start_slot[D.w_off + w];
-        const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) dst[e] = src[e];
-        out_ll = C.logl[D.pt_off + s0];
-    }
-    if (lig == 0) {
-        C.logl[D.pt_off + slot] = out_ll;
-        C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
-        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(nin));
-        atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
-        if (pick <= 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
     }
 }
 

@@ -56,15 +56,6 @@ static cudaError_t hss1_t(const DevCtx &C, const int *runs, int nr, int max_k, c
     return cudaGetLastError();
 }
 template <int G, int E>
-static cudaError_t pick_t(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
-                          cudaStream_t s)
-{
-    const int gpc = HSS_THREADS / G;
-    const int bx = (max_k + gpc - 1) / gpc;
-    k_hss_pick<G, E><<<dim3(bx, nr), HSS_THREADS, 0, s>>>(C, runs, R, rec_base);
-    return cudaGetLastError();
-}
-template <int G, int E>
 static cudaError_t occ_t(size_t smem, int *blocks_per_sm)
 {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, G, E>, HSS_THREADS, smem);
@@ -130,11 +121,6 @@ static cudaError_t hss1(int tile, const DevCtx &C, const int *runs, int nr, int 
                         const long *rec_base, size_t smem, int pis, cudaStream_t s)
 {
     GGNS_DISPATCH(hss1_t, C, runs, nr, max_k, R, rec_base, smem, pis, s)
-}
-static cudaError_t pick(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
-                        const long *rec_base, cudaStream_t s)
-{
-    GGNS_DISPATCH(pick_t, C, runs, nr, max_k, R, rec_base, s)
 }
 static cudaError_t hss1_occ(int tile, size_t smem, int *blocks_per_sm)
 {
