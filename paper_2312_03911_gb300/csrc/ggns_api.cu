@@ -250,6 +250,7 @@ ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int 
     const double log2pi = 1.8378770664093454836;
     lik_const = 0.f;
     if (lk.kind == NS_LIK_ROSENBROCK) return NS_OK;
+    for (int k = K; k < comp_slots(K, lk.kind); ++k) out[L.comp_b + k] = -INFINITY;  // padding: weight 0
     for (int k = 0; k < K; ++k)
         for (int i = 0; i < d; ++i) out[L.means + (long)k * d_pad + i] = (float)lk.means[(size_t)k * d + i];
     for (int k = 0; k < K; ++k) {

@@ -67,15 +67,25 @@ struct RunDesc {
 struct ParLayout {
     long lo, hi, means, comp_a, comp_b, prec, pmu, total;
 };
+// Component slots of the parameter block: an isotropic mixture of up to 8
+// components is padded to 4 or 8 slots (a = 0, b = -inf, mean 0: weight exactly
+// 0), so its likelihood runs over a compile-time count.
+__host__ __device__ inline int comp_slots(int n_comp, int kind)
+{
+    if (kind == NS_LIK_MIX_ISO && n_comp <= 8) return n_comp <= 4 ? 4 : 8;
+    return n_comp;
+}
+
 __host__ __device__ inline ParLayout par_layout(int d, int d_pad, int n_comp, int kind)
 {
     ParLayout L;
     long o = 0;
+    const int ns = comp_slots(n_comp, kind);
     L.lo = o; o += d_pad;
     L.hi = o; o += d_pad;
-    L.means = o; o += (long)n_comp * d_pad;
-    L.comp_a = o; o += n_comp;
-    L.comp_b = o; o += n_comp;
+    L.means = o; o += (long)ns * d_pad;
+    L.comp_a = o; o += ns;
+    L.comp_b = o; o += ns;
     o = (o + 3) & ~3L;
     L.prec = o;
     if (kind == NS_LIK_DENSE_GAUSS || kind == NS_LIK_DENSE_MIX) o += (long)d * d_pad;

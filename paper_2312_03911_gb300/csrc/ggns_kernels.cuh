@@ -64,6 +64,54 @@ __host__ __device__ inline long param_smem_floats(const RunDesc &D, bool prec_in
 // rbuf: per-walker shared scratch of d_pad floats (dense kinds only).
 // resp: optional responsibilities per component (for d/d mu), or nullptr.
 // ------------------------------------------------------------------------
+// Isotropic mixture over KS padded component slots (KS compile-time: straight-line
+// code; padded slots have weight exactly 0).  Distances for every slot, one
+// max, one normalisation; exp, log and the reciprocal use the SFU forms (a few
+// ulp; the log-likelihood is used to FP32 accuracy anyway).
+template <int KS, int G, int E>
+__device__ __forceinline__ float lik_mix_slots(const ParView &P, int dp, const float (&x)[E], float (&g)[E], int c0,
+                                               int K, float *dmu_w)
+{
+    float q[KS], tk[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        q[k] = 0.f;
+        const float *mu = P.means + (long)k * dp + c0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float r = x[e] - mu[e];
+            q[k] = fmaf(r, r, q[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KS; ++k) q[k] = gsum<G>(q[k]);
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        tk[k] = P.b[k] - 0.5f * P.a[k] * q[k];
+        m = fmaxf(m, tk[k]);
+    }
+    float s = 0.f, acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const float wk = __expf(tk[k] - m);
+        s += wk;
+        if (dmu_w && k < K) dmu_w[k] = wk;
+        const float *mu = P.means + (long)k * dp + c0;
+        const float c = -wk * P.a[k];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = fmaf(c, x[e] - mu[e], acc[e]);
+    }
+    const float inv = __fdividef(1.f, s);
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+    if (dmu_w)
+        for (int k = 0; k < K; ++k) dmu_w[k] *= inv;
+    return m + __logf(s);
+}
+
 template <int KIND, int G, int E>
 __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E],
                                           int c0, float *rbuf, float *dmu_w)
@@ -84,56 +132,8 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
     } else if constexpr (KIND == NS_LIK_MIX_ISO) {
         constexpr int KC = 8;
         const int K = D.n_comp;
-        if (K <= KC) {
-            // all components in registers: distances, one max, one normalisation
-            float q[KC], tk[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                q[k] = 0.f;
-                if (k < K) {
-                    const float *mu = P.means + (long)k * dp + c0;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const float r = x[e] - mu[e];
-                        q[k] = fmaf(r, r, q[k]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < KC; ++k)
-                if (k < K) q[k] = gsum<G>(q[k]);
-            float m = -INFINITY;
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                tk[k] = (k < K) ? P.b[k] - 0.5f * P.a[k] * q[k] : -INFINITY;
-                m = fmaxf(m, tk[k]);
-            }
-            float s = 0.f;
-            float acc[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = 0.f;
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                if (k < K) {
-                    const float wk = expf(tk[k] - m);
-                    s += wk;
-                    if (dmu_w) dmu_w[k] = wk;
-                    const float *mu = P.means + (long)k * dp + c0;
-                    const float c = -wk * P.a[k];
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        const float r = x[e] - mu[e];
-                        acc[e] = fmaf(c, r, acc[e]);
-                    }
-                }
-            }
-            const float inv = 1.f / s;
-#pragma unroll
-            for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
-            if (dmu_w)
-                for (int k = 0; k < K; ++k) dmu_w[k] *= inv;
-            return m + logf(s);
-        }
+        if (K <= 4) return lik_mix_slots<4, G, E>(P, dp, x, g, c0, K, dmu_w);
+        if (K <= 8) return lik_mix_slots<8, G, E>(P, dp, x, g, c0, K, dmu_w);
         // more components: online log-sum-exp over chunks of KC
         float m = -INFINITY, s = 0.f;
         float acc[E];
@@ -536,12 +536,12 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         if (stepping && outside) {
             if (outbox > 0) {
                 // reflect off the violated prior-box faces: n = nb / sqrt(#faces)
-                const float c = 2.f * pnb / static_cast<float>(outbox);
+                const float c = __fdividef(2.f * pnb, static_cast<float>(outbox));
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = fmaf(-c, nb[e], p[e]);
             } else if (gg > 0.f && gg <= 3.0e38f) {
                 // p' = p - 2 (p.n) n with n = g / |g|
-                const float c = 2.f * pg / gg;
+                const float c = __fdividef(2.f * pg, gg);
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = fmaf(-c, g[e], p[e]);
             } else {
@@ -753,11 +753,11 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
         }
         if (stepping && outside) {
             if (outbox > 0) {
-                const float cc = 2.f * pnb / static_cast<float>(outbox);
+                const float cc = __fdividef(2.f * pnb, static_cast<float>(outbox));
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = fmaf(-cc, nb[e], p[e]);
             } else if (gg > 0.f && gg <= 3.0e38f) {
-                const float cc = 2.f * pg / gg;
+                const float cc = __fdividef(2.f * pg, gg);
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = fmaf(-cc, g[e], p[e]);
             } else {
