@@ -642,9 +642,12 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
     int w = 0, t = 0, nref = 0, consec = 0;
     bool reg_min = false, reg_max = false;
     bool active = false, exhausted = false;
-    // lane 0 of a group: walkers still to register (read one step ahead) and, once
-    // that reached 0, the final t_stop
+    // walkers still to register (read one step ahead, the same value in every lane
+    // of a group: one load instruction) and, once that reached 0, the final t_stop
     int rem_seen = 1, tstop_final = -1;
+    // this walker's record rows
+    uint2 *rec_meta = nullptr;
+    float *rec_ll = nullptr, *rec_x = nullptr;
     // noise of the next step (it depends only on slot and step, so it is drawn a
     // step ahead, beside the current step's likelihood)
     uint32_t spare = 0;
@@ -670,6 +673,10 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
                 t = nref = consec = 0;
                 rem_seen = 1;
                 tstop_final = -1;
+                const long row0 = rb + (long)w * R.rec_len;
+                rec_meta = R.meta + row0;
+                rec_ll = R.ll + row0;
+                rec_x = R.x + row0 * R.xs + c0;
                 // archive the dead point that this walker's output will replace
                 const int ks = C.order[D.pt_off + w];
                 const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
@@ -690,34 +697,25 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
         }
         if (active) {
             // stop once every walker has met its stop rule and this one has reached t_stop,
-            // or at the record length / step cap
-            int stop = 0;
-            if (lig == 0) {
-                if (reg_max && rem_seen == 0 && tstop_final < 0) {
-                    // every walker has registered: t_stop is final (read after the count)
-                    __threadfence();
-                    tstop_final = *v_tstop;
-                }
-                if (t >= L) {
-                    stop = 1;
-                    if (!(tstop_final >= 0 && t >= tstop_final) && L < D.n_steps) {
-                        // the stop may not be known yet: decide on fresh values
-                        const int rem_now = *v_remain;
-                        __threadfence();
-                        if (!(reg_max && rem_now == 0 && t >= *v_tstop)) S->rec_overflow = 1;
-                    }
-                } else if (tstop_final >= 0 && t >= tstop_final) {
-                    stop = 1;
-                }
+            // or at the record length / step cap (every lane of the group decides alike)
+            if (reg_max && rem_seen == 0 && tstop_final < 0) {
+                // every walker has registered: t_stop is final (read after the count)
+                __threadfence();
+                tstop_final = *v_tstop;
             }
-            stop = __shfl_sync(gmask, stop, gbase);
-            if (stop) active = false;
+            const bool at_stop = tstop_final >= 0 && t >= tstop_final;
+            if (t >= L && !at_stop && L < D.n_steps && lig == 0) {
+                // the stop may not be known yet: decide on fresh values
+                const int rem_now = *v_remain;
+                __threadfence();
+                if (!(reg_max && rem_now == 0 && t >= *v_tstop)) S->rec_overflow = 1;
+            }
+            if (at_stop || t >= L) active = false;
         }
-        __syncwarp();
         if (!__any_sync(0xffffffffu, active || !exhausted)) break;
         const bool stepping = active;
         // the registration count for the next stop test, read while this step runs
-        if (lig == 0 && stepping && reg_max && rem_seen != 0) rem_seen = *v_remain;
+        if (stepping && reg_max && rem_seen != 0) rem_seen = *v_remain;
 
         // ---- one step of Algorithm 5 (as in k_hss)
         const int ts = t + 1;
@@ -776,21 +774,26 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;
             // record the step
-            const long row = rb + (long)w * R.rec_len + (ts - 1);
             if (!outside) {
-                float *dst = R.x + row * R.xs + c0;
 #pragma unroll
-                for (int e = 0; e < E; ++e) dst[e] = x[e];
+                for (int e = 0; e < E; ++e) rec_x[e] = x[e];
             }
             if (lig == 0) {
-                R.meta[row] = make_uint2(res_word, outside ? 1u : 0u);
-                R.ll[row] = ll;
-                if (!reg_min && (nref >= D.min_ref || ts >= D.n_steps)) {
+                *rec_meta = make_uint2(res_word, outside ? 1u : 0u);
+                *rec_ll = ll;
+            }
+            rec_x += R.xs;
+            ++rec_meta;
+            ++rec_ll;
+            const bool reg_min_now = !reg_min && (nref >= D.min_ref || ts >= D.n_steps);
+            const bool reg_max_now = !reg_max && ((nref >= D.max_ref && ts >= D.min_steps) || ts >= D.n_steps);
+            if (lig == 0 && (reg_min_now || reg_max_now)) {
+                if (reg_min_now) {
                     atomicMax(&S->t_save1, (nref >= D.min_ref) ? ts : D.n_steps + 1);
                     __threadfence();
                     atomicSub(&S->remain_min, 1);
                 }
-                if (!reg_max && ((nref >= D.max_ref && ts >= D.min_steps) || ts >= D.n_steps)) {
+                if (reg_max_now) {
                     atomicMax(&S->t_stop1, ts);
                     __threadfence();
                     atomicSub(&S->remain_max, 1);
