@@ -51,6 +51,7 @@ namespace {
 
 constexpr int GRAPH_ITERS = 8;
 constexpr size_t SMEM_LIMIT = 200 * 1024;
+constexpr int NOISE_BLOCKS_PER_RUN = 64;
 
 struct RunClass {
     int kind, tile;
@@ -76,6 +77,9 @@ struct Group {
     // the statistics update runs on a second stream, beside the HSS phases
     cudaStream_t ev_stream = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // the momentum noise of the single-pass HSS is drawn on a third stream
+    cudaStream_t nz_stream = nullptr;
+    cudaEvent_t nz_fork_ev = nullptr, nz_join_ev = nullptr;
     int launches_per_iter = 0;
 };
 
@@ -344,14 +348,49 @@ ns_status ensure_dead_capacity(ns_ctx *ctx, int iters, const std::vector<RunStat
     return NS_OK;
 }
 
-ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
+// The termination test of the previous iteration, once its statistics are in.
+ns_status launch_term_join(ns_ctx *ctx, Group &g, cudaStream_t s)
+{
+    CU(cudaStreamWaitEvent(s, g.join_ev, 0));
+    CU(launch_term(ctx->dc, g.r0, g.nr, s));
+    return NS_OK;
+}
+
+// One iteration of Algorithm 3 for the runs of group g.  Unless `first`, the
+// previous iteration's statistics (on the second stream) are joined after this
+// iteration's k-NN, and its termination test runs then; a launch sequence ends
+// with launch_term_join.
+ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, bool first)
 {
     const DevCtx &C = ctx->dc;
     int n = 0;
+    bool any_single = false;
+    for (auto &cl : g.classes) any_single |= (cl.single != 0);
+    const bool noise_ahead = any_single && ctx->rec.nT > 0;
+    if (noise_ahead) {
+        // fork: this iteration's momentum noise beside cluster finding and selection
+        CU(cudaEventRecord(g.nz_fork_ev, s));
+        CU(cudaStreamWaitEvent(g.nz_stream, g.nz_fork_ev, 0));
+        for (auto &cl : g.classes)
+            if (cl.single) {
+                CU(launch_noise(C, cl.runs_dev, (int)cl.runs.size(), NOISE_BLOCKS_PER_RUN, ctx->rec, ctx->rec_base_dev,
+                                g.nz_stream));
+                ++n;
+            }
+        CU(cudaEventRecord(g.nz_join_ev, g.nz_stream));
+    }
     if (ctx->any_clustering) {
         CU(launch_knn(C, g.r0, g.nr, g.max_n, ctx->knn_smem, s));
+        ++n;
+    }
+    if (!first) {
+        ns_status ts = launch_term_join(ctx, g, s);
+        if (ts != NS_OK) return ts;
+        ++n;
+    }
+    if (ctx->any_clustering) {
         CU(launch_cluster(C, g.r0, g.nr, ctx->lastkey, ctx->cl_smem, s));
-        n += 2;
+        ++n;
     }
     CU(launch_sort(C, g.r0, g.nr, ctx->sort_smem, s));
     ++n;
@@ -362,6 +401,7 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
     CU(cudaEventRecord(g.join_ev, g.ev_stream));
     ++n;
     if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][0], s, cudaEventRecordExternal));
+    if (noise_ahead) CU(cudaStreamWaitEvent(s, g.nz_join_ev, 0));
     // single pass where every walker block of the class is resident, then the
     // three phases (for single-pass classes only if the records overflowed)
     for (auto &cl : g.classes)
@@ -383,8 +423,6 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot)
             ++n;
         }
     if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][1], s, cudaEventRecordExternal));
-    // join before the tail: termination reads the statistics
-    CU(cudaStreamWaitEvent(s, g.join_ev, 0));
     CU(launch_tail(C, g.r0, g.nr, s));
     ++n;
     g.launches_per_iter = n;
@@ -700,6 +738,16 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 CU(cudaMemcpy(ctx->rec_base_dev, base.data(), sizeof(long) * n_runs, cudaMemcpyHostToDevice));
                 ctx->rec.rec_len = (int)rec_len;
                 ctx->rec.xs = xs;
+                // noise drawn ahead: GGNS_NOISE_STEPS steps per walker (default 128, 0: off)
+                long nT = 128;
+                if (const char *v = getenv("GGNS_NOISE_STEPS")) nT = std::max(0, atoi(v));
+                nT = std::min<long>(nT, rec_len);
+                if (xs % 4 != 0 || walkers * nT * ((long)xs * 4 + 4) > budget) nT = 0;
+                if (nT > 0) {
+                    CU(cudaMalloc(&ctx->rec.nz, sizeof(float) * walkers * nT * xs));
+                    CU(cudaMalloc(&ctx->rec.nsp, sizeof(uint32_t) * walkers * nT));
+                }
+                ctx->rec.nT = (int)nT;
                 return NS_OK;
             };
             CK(mkrec());
@@ -750,6 +798,9 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 }
                 CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
                 CU(cudaStreamCreateWithFlags(&g.ev_stream, cudaStreamNonBlocking));
+                CU(cudaStreamCreateWithFlags(&g.nz_stream, cudaStreamNonBlocking));
+                CU(cudaEventCreateWithFlags(&g.nz_fork_ev, cudaEventDisableTiming));
+                CU(cudaEventCreateWithFlags(&g.nz_join_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.fork_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.join_ev, cudaEventDisableTiming));
                 for (int i = 0; i < GRAPH_ITERS; ++i)
@@ -803,12 +854,18 @@ ns_status ns_step(ns_ctx *ctx, int n_iters, int *done)
     if (s != NS_OK) return s;
     s = ensure_dead_capacity(ctx, n_iters, st);
     if (s != NS_OK) return s;
-    for (int i = 0; i < n_iters; ++i)
-        for (auto &g : ctx->groups) {
-            s = launch_iteration(ctx, g, ctx->stream, -1);
+    for (auto &g : ctx->groups) {
+        for (int i = 0; i < n_iters; ++i) {
+            s = launch_iteration(ctx, g, ctx->stream, -1, i == 0);
             if (s != NS_OK) return s;
             ctx->launches += g.launches_per_iter;
         }
+        if (n_iters > 0) {
+            s = launch_term_join(ctx, g, ctx->stream);
+            if (s != NS_OK) return s;
+            ++ctx->launches;
+        }
+    }
     s = read_states(ctx, st);
     if (s != NS_OK) return s;
     int all = 1;
@@ -829,11 +886,16 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
         cudaGraph_t gr;
         CU(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
         for (int i = 0; i < GRAPH_ITERS; ++i) {
-            s = launch_iteration(ctx, g, g.stream, i);
+            s = launch_iteration(ctx, g, g.stream, i, i == 0);
             if (s != NS_OK) {
                 cudaStreamEndCapture(g.stream, &gr);
                 return s;
             }
+        }
+        s = launch_term_join(ctx, g, g.stream);
+        if (s != NS_OK) {
+            cudaStreamEndCapture(g.stream, &gr);
+            return s;
         }
         CU(cudaStreamEndCapture(g.stream, &gr));
         CU(cudaGraphInstantiate(&g.graph, gr, 0));
@@ -1160,6 +1222,9 @@ void ns_destroy(ns_ctx *ctx)
         if (g.join_ev) cudaEventDestroy(g.join_ev);
         if (g.stream) cudaStreamDestroy(g.stream);
         if (g.ev_stream) cudaStreamDestroy(g.ev_stream);
+        if (g.nz_stream) cudaStreamDestroy(g.nz_stream);
+        if (g.nz_fork_ev) cudaEventDestroy(g.nz_fork_ev);
+        if (g.nz_join_ev) cudaEventDestroy(g.nz_join_ev);
     }
     if (ctx->start_ev) cudaEventDestroy(ctx->start_ev);
     for (auto &rc : ctx->classes)
@@ -1182,6 +1247,8 @@ void ns_destroy(ns_ctx *ctx)
     if (ctx->rec.meta) cudaFree(ctx->rec.meta);
     if (ctx->rec.ll) cudaFree(ctx->rec.ll);
     if (ctx->rec.x) cudaFree(ctx->rec.x);
+    if (ctx->rec.nz) cudaFree(ctx->rec.nz);
+    if (ctx->rec.nsp) cudaFree(ctx->rec.nsp);
     if (ctx->rec_base_dev) cudaFree(ctx->rec_base_dev);
     if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
     delete ctx;

@@ -32,7 +32,22 @@ struct RecView {
     float *x;
     int rec_len;  // records per walker
     int xs;       // floats per x record (the largest d_pad of the batch)
+    // momentum noise drawn ahead by k_noise: normals z[(walker row * nT + step - 1) * xs + c]
+    // and the reservoir words sp[walker row * nT + step - 1]; nT = 0: drawn in the walk
+    float *nz;
+    uint32_t *nsp;
+    int nT;
+    int pad_;
 };
+
+// Steps of noise drawn ahead for an iteration: all nT for the first iteration,
+// then 1.5 x the previous t_stop + 16 (at most nT); later steps draw inline.
+__host__ __device__ inline int noise_steps(int nT, int t_stop_last)
+{
+    if (t_stop_last <= 0) return nT;
+    const int n = t_stop_last + t_stop_last / 2 + 16;
+    return n < nT ? n : nT;
+}
 
 // Constant description of one run (device copy, read by every kernel).
 struct RunDesc {
@@ -112,6 +127,9 @@ struct RunState {
     int rec_overflow;      // single-pass HSS ran out of record length: redo in three phases
     unsigned int wcount1;  // single-pass HSS walker refill counter
     int t_save1, t_stop1;  // single-pass HSS window
+    int t_stop_last;       // t_stop of the previous iteration (sizes the noise drawn ahead)
+    int term_pending;      // the iteration's tail ran; its termination test waits for the statistics
+    float lmax_live;       // L_max over the live points after the iteration (classic termination)
     int n_rec_overflow;    // iterations redone in three phases
     int kill_cnt[CMAX];    // kills per cluster in the current iteration
     int spawn_cnt[CMAX];   // new points per cluster in the current iteration

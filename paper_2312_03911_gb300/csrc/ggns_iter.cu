@@ -839,6 +839,24 @@ __global__ void k_tail(DevCtx C, int r0)
     S->n_like += (long)D.k * S->t_stop;
     S->n_steps_total += (long)D.k * S->t_stop;
     S->n_rec_overflow += S->rec_overflow;
+    S->lmax_live = m;
+    S->iter += 1;
+    S->term_pending = 1;
+}
+
+// Termination test of the last finished iteration (Algorithm 3): runs once its
+// FP64 statistics are in, which lets them overlap the tail and the next
+// iteration's k-NN.  XL peak on the dead-point sequence (termination 0) or
+// X L_max < tol Z (termination 1); then the iteration cap.
+__global__ void k_term(DevCtx C, int r0, int n_runs)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_runs) return;
+    const int r = r0 + t;
+    const RunDesc &D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done || !S->term_pending) return;
+    S->term_pending = 0;
     if (S->log_xl > S->log_xl_max) S->log_xl_max = S->log_xl;
     bool stop;
     if (D.termination == 0) {
@@ -848,9 +866,8 @@ __global__ void k_tail(DevCtx C, int r0)
         const Stats *st = C.stats + r;
         for (int c = 0; c < CMAX; ++c)
             if (st->alive[c]) lx = log_add(lx, st->logXp[c]);
-        stop = (lx + (double)m) < D.log_tol + S->logz;
+        stop = (lx + (double)S->lmax_live) < D.log_tol + S->logz;
     }
-    S->iter += 1;
     if (S->n_clusters > S->max_clusters) S->max_clusters = S->n_clusters;
     if (stop) {
         S->terminated = 1;
@@ -883,6 +900,7 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         // the tail and the counters read the window of the three-phase form
         S->t_save = S->t_save1;
         S->t_stop = S->t_stop1;
+        S->t_stop_last = S->t_stop1;
     }
     if (w >= W) return;
     const long base = rec_base[r] + (long)w * R.rec_len;
@@ -967,19 +985,25 @@ __device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d
     return s;
 }
 
+// Cluster sizes from the labels (every CTA counts them itself: n reads).
+__device__ void knn_label_counts(int n, const int *label, int *s_cnt /* [CMAX] */)
+{
+    if (threadIdx.x < CMAX) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[label[i]], 1);
+    __syncthreads();
+}
+
 // Queries of one CTA, grouped by label.  The n points are ordered by (label,
 // index); CTA b takes positions [32 b, 32 b + 32) of that order, so its queries
 // come from one or two clusters and it scans only candidates with those labels.
 // q_slot[32] receives the query indices (-1 past n); returns the label set as a
-// bit mask.  Every CTA computes the label counts itself (n reads).
-__device__ unsigned long long knn_block_queries(int n, const int *label, int *q_slot, int *s_cnt /* [CMAX] */,
+// bit mask.  s_cnt: the label counts.
+__device__ unsigned long long knn_block_queries(int n, const int *label, int *q_slot, const int *s_cnt,
                                                 int *s_wsum /* [KQ_WARPS] */)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < CMAX) s_cnt[tid] = 0;
     if (tid < 32) q_slot[tid] = -1;
-    __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) atomicAdd(&s_cnt[label[i]], 1);
     __syncthreads();
     const int p0 = blockIdx.x * 32, p1 = min(p0 + 32, n);
     unsigned long long mask = 0;
@@ -1029,10 +1053,10 @@ template <int QR>
 __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
                           unsigned long long *merge /* [KQ_WARPS][32][KQ_MSTRIDE] */,
                           float *tile /* [KQ_TILE][QR] */, int *tidx /* [KQ_TILE] */, int *tlab /* [KQ_TILE] */,
-                          int *q_slot /* [32] */, int *s_cnt /* [CMAX] */, int *s_wsum /* [KQ_WARPS] */)
+                          int *q_slot /* [32] */, int *s_wsum /* [KQ_WARPS] */)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long lmask = knn_block_queries(n, label, q_slot, s_cnt, s_wsum);
+    const unsigned long long lmask = knn_block_queries(n, label, q_slot, csize, s_wsum);
     const int i = q_slot[lane];
     const bool act = i >= 0;
     const int li = act ? label[i] : -1;
@@ -1197,9 +1221,9 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
 }
 
 // shared memory: merge lists [KQ_WARPS][32][KQ_MSTRIDE] u64 | tile [KQ_TILE][64] f32 | tile indices and
-// labels [KQ_TILE] | query slots [32] | label counts [CMAX] | warp sums [KQ_WARPS]
-__device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
-                         float *smem)
+// labels [KQ_TILE] | query slots [32] | label counts [CMAX] | warp sums [KQ_WARPS].  The cluster sizes
+// come from the labels themselves, so the k-NN may run while the statistics are being updated.
+__device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, int *nbr, float *smem)
 {
     unsigned long long *merge = reinterpret_cast<unsigned long long *>(smem);
     float *tile = reinterpret_cast<float *>(merge + KQ_WARPS * 32 * KQ_MSTRIDE);
@@ -1208,11 +1232,12 @@ __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *l
     int *q_slot = tlab + KQ_TILE;
     int *s_cnt = q_slot + 32;
     int *s_wsum = s_cnt + CMAX;
-    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
-    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
-    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
-    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, csize, nbr, merge, tile, tidx, tlab, q_slot, s_cnt, s_wsum);
-    else knn_lanes_wide(x, xstride, n, d, label, csize, nbr, merge);
+    knn_label_counts(n, label, s_cnt);
+    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else knn_lanes_wide(x, xstride, n, d, label, s_cnt, nbr, merge);
 }
 
 __global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
@@ -1222,7 +1247,7 @@ __global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
     const RunDesc &D = C.desc[r];
     if (C.state[r].done || !D.clustering) return;
     const int d = D.d;
-    knn_rows(C.fa + D.x_off, D.d_pad, D.n_live, d, C.label + D.pt_off, C.stats[r].n, C.nbr + D.nbr_off, ksm);
+    knn_rows(C.fa + D.x_off, D.d_pad, D.n_live, d, C.label + D.pt_off, C.nbr + D.nbr_off, ksm);
 }
 
 size_t knn_smem_bytes(int d)
@@ -1558,11 +1583,10 @@ __global__ void __launch_bounds__(SEL_THREADS) k_sort_logl(const float *logl, in
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (int)(skeys[i] & 0xffffffffu);
 }
 
-__global__ void __launch_bounds__(KQ_WARPS * 32) k_knn_plain(const float *x, int n, int d, const int *label,
-                                                              const int *csize, int *nbr)
+__global__ void __launch_bounds__(KQ_WARPS * 32) k_knn_plain(const float *x, int n, int d, const int *label, int *nbr)
 {
     extern __shared__ float ksm[];
-    knn_rows(x, d, n, d, label, csize, nbr, ksm);
+    knn_rows(x, d, n, d, label, nbr, ksm);
 }
 
 __global__ void __launch_bounds__(CL_THREADS) k_components_plain(const float *x, int n, int d, const int *label,
@@ -1654,10 +1678,54 @@ cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaS
     k_final<<<n_runs, SEL_THREADS, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
+// Momentum noise of the single-pass HSS, drawn ahead of the walk (the same
+// Philox blocks and Box-Muller pairs the walker would draw): one thread per
+// (walker, step, block of four components).
+constexpr int NOISE_THREADS = 256;
+
+__global__ void __launch_bounds__(NOISE_THREADS) k_noise(DevCtx C, const int *run_list, RecView R, const long *rec_base)
+{
+    const int r = run_list[blockIdx.y];
+    const RunDesc &D = C.desc[r];
+    const RunState *S = C.state + r;
+    if (S->done) return;
+    if (D.d_pad & 3) return;      // drawn in the walk (no whole blocks of four components)
+    const int nb = D.d_pad >> 2;  // blocks of four components
+    const int steps = noise_steps(R.nT, S->t_stop_last);
+    const long items = (long)D.k * steps * nb;
+    const uint32_t iter = (uint32_t)S->iter;
+    const long wrow0 = rec_base[r] / R.rec_len;  // first walker row of this run
+    for (long it = (long)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(it % nb);
+        const long ws = it / nb;
+        const int ts = (int)(ws % steps) + 1;
+        const int w = (int)(ws / steps);
+        const U4 wd = rng_block(D, iter, P_NOISE, (uint32_t)w, (uint32_t)ts, (uint32_t)b);
+        float4 z;
+        box_muller(wd.x, wd.y, z.x, z.y);
+        box_muller(wd.z, wd.w, z.z, z.w);
+        const long row = (wrow0 + w) * R.nT + (ts - 1);
+        *reinterpret_cast<float4 *>(R.nz + row * R.xs + 4 * b) = z;
+        if (b == 0) R.nsp[row] = spare_bits(wd);
+    }
+}
+
+cudaError_t launch_noise(const DevCtx &C, const int *runs, int nr, int blocks_per_run, const RecView &R,
+                         const long *rec_base, cudaStream_t s)
+{
+    k_noise<<<dim3(blocks_per_run, nr), NOISE_THREADS, 0, s>>>(C, runs, R, rec_base);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
                             cudaStream_t s)
 {
     k_hss_pick<<<dim3((max_k + PICK_WARPS - 1) / PICK_WARPS, nr), PICK_WARPS * 32, 0, s>>>(C, runs, R, rec_base);
+    return cudaGetLastError();
+}
+cudaError_t launch_term(const DevCtx &C, int r0, int n_runs, cudaStream_t s)
+{
+    k_term<<<(n_runs + 127) / 128, 128, 0, s>>>(C, r0, n_runs);
     return cudaGetLastError();
 }
 cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s)
@@ -1720,7 +1788,7 @@ cudaError_t launch_knn_components(const float *x, int n, int d, const int *label
     const size_t ks = knn_smem_bytes(d);
     cudaError_t e = set_max_smem((const void *)k_knn_plain, ks);
     if (e != cudaSuccess) return e;
-    k_knn_plain<<<(n + 31) / 32, KQ_WARPS * 32, ks, s>>>(x, n, d, label, csize, nbr);
+    k_knn_plain<<<(n + 31) / 32, KQ_WARPS * 32, ks, s>>>(x, n, d, label, nbr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t cs = sizeof(int) * (size_t)n;

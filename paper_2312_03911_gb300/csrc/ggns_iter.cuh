@@ -25,8 +25,11 @@ cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t c
 cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
+cudaError_t launch_noise(const DevCtx &C, const int *runs, int nr, int blocks_per_run, const RecView &R,
+                         const long *rec_base, cudaStream_t s);
 cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                             const long *rec_base, cudaStream_t s);
+cudaError_t launch_term(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
 cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
 cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s);
 cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,

@@ -618,6 +618,8 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
     float *rbase = smem + param_smem_floats(D, prec_in_smem);
     __syncthreads();
     const long rb = rec_base[r];  // first record row of this run
+    const int nsteps = (D.d_pad & 3) ? 0 : noise_steps(R.nT, S->t_stop_last);
+    const long nrow0 = (rb / R.rec_len) * R.nT;  // first noise row of this run
     const int lane = threadIdx.x & 31;
     const int lig = lane % G;
     const int gbase = lane - lig;
@@ -669,7 +671,15 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
                 lane_normals<E>(D, iter, P_MOM, w, 0, c0, p);
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] *= vmask[e];
-                lane_normals<E>(D, iter, P_NOISE, w, 1, c0, eps, &spare);
+                if (nsteps >= 1) {
+                    const long nr0 = nrow0 + (long)w * R.nT;
+                    const float *src = R.nz + nr0 * R.xs + c0;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) eps[e] = src[e];
+                    spare = R.nsp[nr0];
+                } else {
+                    lane_normals<E>(D, iter, P_NOISE, w, 1, c0, eps, &spare);
+                }
                 t = nref = consec = 0;
                 rem_seen = 1;
                 tstop_final = -1;
@@ -723,7 +733,16 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
         float ecur[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) ecur[e] = eps[e];
-        lane_normals<E>(D, iter, P_NOISE, w, ts + 1, c0, eps, &spare);
+        if (ts + 1 <= nsteps) {
+            // drawn ahead; the load completes while this step runs
+            const long nr1 = nrow0 + (long)w * R.nT + ts;
+            const float *src = R.nz + nr1 * R.xs + c0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) eps[e] = src[e];
+            spare = R.nsp[nr1];
+        } else {
+            lane_normals<E>(D, iter, P_NOISE, w, ts + 1, c0, eps, &spare);
+        }
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);

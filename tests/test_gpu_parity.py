@@ -326,24 +326,27 @@ def test_single_pass_hss_equals_three_phases(kind, d, n, monkeypatch):
 
 
 def test_single_pass_runs_equal_three_phase_runs(monkeypatch):
-    """Whole clustered runs: the single-pass HSS (with and without record overflows)
-    reproduces the three-phase runs exactly."""
+    """Whole clustered runs: the single-pass HSS (with and without record overflows, with
+    the momentum noise drawn ahead for all, a few or none of the steps) reproduces the
+    three-phase runs exactly."""
     ws = [W.small_workload("mix", 8, 300, seed=23, clustering=1), W.small_workload("iso", 5, 120, seed=24)]
     out = {}
-    for mode, rec_len in ((3, None), (0, None), (0, 4)):
+    cases = ((3, None, None), (0, None, None), (0, 4, None), (0, None, 6), (0, None, 0))
+    for mode, rec_len, noise in cases:
         monkeypatch.setenv("GGNS_HSS", str(mode))
-        if rec_len is None:
-            monkeypatch.delenv("GGNS_REC_LEN", raising=False)
-        else:
-            monkeypatch.setenv("GGNS_REC_LEN", str(rec_len))
+        for var, val in (("GGNS_REC_LEN", rec_len), ("GGNS_NOISE_STEPS", noise)):
+            if val is None:
+                monkeypatch.delenv(var, raising=False)
+            else:
+                monkeypatch.setenv(var, str(val))
         s, res = _run_gpu(ws)
         prof = s.profile()
-        out[(mode, rec_len)] = (res, [s.samples(r) for r in range(len(ws))], prof)
-    ref_res, ref_smp, ref_prof = out[(3, None)]
+        out[(mode, rec_len, noise)] = (res, [s.samples(r) for r in range(len(ws))], prof)
+    ref_res, ref_smp, ref_prof = out[cases[0]]
     assert ref_prof["rec_len"] == 0
-    assert out[(0, None)][2]["rec_len"] > 0
-    assert out[(0, 4)][2]["rec_overflows"] > 0
-    for key in ((0, None), (0, 4)):
+    assert out[cases[1]][2]["rec_len"] > 0
+    assert out[cases[2]][2]["rec_overflows"] > 0
+    for key in cases[1:]:
         res, smp, _ = out[key]
         for a, b in zip(res, ref_res):
             assert a == b
