@@ -39,32 +39,32 @@ UNIT = "point-steps/s"
 WORKLOAD = "c2"
 DEFAULT_REPLICAS = 17
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per k_hss launch from one ncu capture of this workload
-# (profiles/k_hss_c2x17.md), valid only for the kernel sources with these hashes.
-HSS_TRAFFIC_BYTES = 3.364e6
-HSS_TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "88ed08405d6fdc41",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "f19a947a9ee78cc9"}
+# DRAM bytes (read + write) per k_hss1 launch from one ncu capture of this workload
+# (profiles/k_hss1_c2x17.md), valid only for the kernel sources with these hashes.
+HSS_TRAFFIC_BYTES = 132.13e6
+HSS_TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "872a85ff6b26ff9b",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "c7e00a083f5c644f"}
 SMS = 152
 FP32_LANES_PER_SM = 128
 
 
-def lane_ops_per_point_step(d: int, K: int, out_frac: float) -> float:
+def lane_ops_per_point_step(d: int, K: int, out_frac: float, rng: bool = True) -> float:
     """Algorithmic lane operations of one walker step of the isotropic-mixture HSS
     (the per-unit figure of the roofline; derivation in the design notes):
     move d FMA; likelihood 2Kd (difference, FMA) + K exp + 1 log + 12 scalar;
-    score Kd FMA + d scale; box test 2d; reflection 3d on outside steps;
-    d normals: d/4 Philox4x32-10 blocks x 100 integer ops + 4 ops per
-    uniform + 4 ops per normal (log/sqrt/sincos shared by pairs); noise d FMA;
-    reservoir word: one Philox block."""
+    score Kd FMA + d scale; box test 2d; reflection 3d on outside steps; noise
+    2d (scale, FMA).  With rng: the step's d normals, d/4 Philox4x32-10 blocks x
+    100 integer ops + 4 ops per uniform + 4 ops per normal (log/sqrt/sincos
+    shared by pairs); the reservoir word rides on the noise block's spare bits.
+    Without rng: the normals were drawn ahead by k_noise."""
     move = d
     lik = 2 * K * d + K + 1 + 12
     score = K * d + d
     box = 2 * d
     refl = 3 * d * out_frac
-    rng = (d / 4) * 100 + 4 * d + 4 * d
-    noise = d
-    res = 100
-    return move + lik + score + box + refl + rng + noise + res
+    noise = 2 * d
+    draw = (d / 4) * 100 + 4 * d + 4 * d if rng else 0.0
+    return move + lik + score + box + refl + noise + draw
 
 
 class ClockSampler:
@@ -285,7 +285,8 @@ def gpu_arm(args):
     # roofline of the dominant kernel (HSS): algorithmic lane-ops / HSS time
     zall = np.array(logz)
     out_frac_est = 0.12
-    ops = lane_ops_per_point_step(32, 4, out_frac_est)
+    drawn_ahead = prof.get("noise_steps", 0) > 0
+    ops = lane_ops_per_point_step(32, 4, out_frac_est, rng=not drawn_ahead)
     hss_s = prof["hss_ms"] / 1000.0  # time during which HSS kernels of any run were executing
     achieved = ops * (sum(pts)) / hss_s if hss_s > 0 else None
     f_sm = (clocks.get("sm_mhz") or 1447.0) * 1e6
@@ -296,6 +297,9 @@ def gpu_arm(args):
             "traffic_unit": "bytes per launch (DRAM read + write)",
             "kernel": ("k_hss1 + k_hss_pick (single pass)" if prof.get("rec_len", 0) > 0 else "k_hss (phases 0-2)"),
             "hss_rec_overflows": prof.get("rec_overflows"), "ops_per_point_step": ops,
+            "noise": ("drawn ahead by k_noise on a second stream (not in this kernel's count): "
+                      f"{lane_ops_per_point_step(32, 4, 0.0) - lane_ops_per_point_step(32, 4, 0.0, rng=False):.0f} "
+                      "lane-ops per point-step") if drawn_ahead else "drawn in the walk",
             "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
             "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}

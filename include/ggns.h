@@ -137,15 +137,16 @@ ns_status ns_run(ns_ctx *ctx, long max_iters);
  * Used to repeat a workload without allocating.  Synchronises. */
 ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
 
-/* Profiling counters of ctx (out[7]): out[0] milliseconds during which at
+/* Profiling counters of ctx (out[8]): out[0] milliseconds during which at
  * least one HSS kernel of ns_run was executing (union over the run groups of
  * the intervals between CUDA events recorded around the HSS kernels of each
  * iteration), out[1] group-iterations measured, out[2] kernels launched by
  * ctx, out[3] rounds of graph replays, out[4] the summed (not merged) HSS
  * intervals, out[5] iterations (summed over runs, since the last restart) whose
  * single-pass HSS ran out of step records and was redone in three phases,
- * out[6] step records per walker (0: the three-phase form only).  reset != 0
- * zeroes out[0..4] after reading.  Synchronises. */
+ * out[6] step records per walker (0: the three-phase form only), out[7] steps
+ * of momentum noise drawn ahead per walker (0: drawn during the walk).
+ * reset != 0 zeroes out[0..4] after reading.  Synchronises. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 
 typedef struct {
@@ -210,6 +211,13 @@ ns_status ns_philox(const uint32_t *ctr_dev, uint32_t key0, uint32_t key1, uint3
  * one of run 0 of ctx.  This is the fused forward used by the walkers. */
 ns_status ns_lik_forward(const ns_ctx *ctx, const float *x_dev, long n, float *logl_dev, float *grad_dev,
                          void *stream);
+
+/* Replace the component means of run `run` by means_host[n_comp][d] (FP64,
+ * row-major; copied before return): the parameters theta of the likelihood
+ * whose log Z gradient the paper's problem statement asks for (Section 2.1).
+ * ns_lik_forward / ns_lik_backward use them at once; sampling uses them after
+ * ns_restart.  NS_ERR_ARG for ROSENBROCK (no means).  Synchronises. */
+ns_status ns_set_means(ns_ctx *ctx, int run, const double *means_host);
 
 /* Adjoint of ns_lik_forward: given gout_dev[n] = d(loss)/d(log L_i),
  * gx_dev[n][d] = gout_i * d log L_i / dx_i and gmu_dev[n_comp][d] =

@@ -96,7 +96,7 @@ struct ns_ctx {
     int n_runs = 0;
     std::vector<RunDesc> desc;
     std::vector<DeadHost> dead;
-    std::vector<std::vector<double>> means64;  // FP64 master copies for the host-side checks
+    std::vector<std::vector<double>> prec64;  // FP64 precision of dense mixtures (P mu_k on new means)
     DevCtx dc{};
     RunDesc *desc_dev = nullptr;
     RunState *state_dev = nullptr;
@@ -585,6 +585,9 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
             delete ctx;
             return s;
         }
+        ctx->prec64.emplace_back();
+        if (lik[r].kind == NS_LIK_DENSE_MIX)
+            ctx->prec64.back().assign(lik[r].precision, lik[r].precision + (size_t)D.d * D.d);
         D.x_off = fa;
         fa += (long)D.n_live * D.d_pad;
         D.ws_off = fa;
@@ -1003,6 +1006,7 @@ ns_status ns_profile(const ns_ctx *cctx, double *out, int reset)
     for (auto &x : st) over += x.n_rec_overflow;
     out[5] = (double)over;
     out[6] = ctx->rec.rec_len;
+    out[7] = ctx->rec.nT;
     if (reset) {
         ctx->hss_ms = ctx->hss_ms_sum = 0.0;
         ctx->hss_iters = ctx->launches = ctx->replays = 0;
@@ -1283,6 +1287,36 @@ static ns_status lik_points(const ns_ctx *cctx, const float *x, long n, int mode
     if (gmu) CU(cudaMemsetAsync(gmu, 0, sizeof(float) * (size_t)D.n_comp * D.d, s));
     CU(kind_launch(D.kind).lik_points(D.tile, ctx->dc, 0, x, n, mode, logl, grad, gout, gmu, rc.smem, rc.prec_in_smem, s));
     CU(cudaStreamSynchronize(s));
+    return NS_OK;
+}
+
+ns_status ns_set_means(ns_ctx *ctx, int run, const double *means_host)
+{
+    if (!ctx || !means_host || run < 0 || run >= ctx->n_runs) return NS_ERR_ARG;
+    const RunDesc &D = ctx->desc[run];
+    if (D.kind == NS_LIK_ROSENBROCK) return fail(ctx, NS_ERR_ARG, "ROSENBROCK has no means");
+    const int K = D.n_comp, d = D.d, dp = D.d_pad;
+    const ParLayout L = par_layout(d, dp, K, D.kind);
+    std::vector<float> m((size_t)K * dp, 0.f);
+    for (int k = 0; k < K; ++k)
+        for (int i = 0; i < d; ++i) m[(size_t)k * dp + i] = (float)means_host[(size_t)k * d + i];
+    CU(cudaMemcpyAsync(ctx->fa + D.par_off + L.means, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    std::vector<float> pm;
+    if (D.kind == NS_LIK_DENSE_MIX) {
+        // P mu_k in FP64 from the master precision, as at creation
+        const std::vector<double> &P = ctx->prec64[run];
+        pm.assign((size_t)K * dp, 0.f);
+        for (int k = 0; k < K; ++k)
+            for (int i = 0; i < d; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < d; ++j) acc += P[(size_t)i * d + j] * means_host[(size_t)k * d + j];
+                pm[(size_t)k * dp + i] = (float)acc;
+            }
+        CU(cudaMemcpyAsync(ctx->fa + D.par_off + L.pmu, pm.data(), sizeof(float) * pm.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
     return NS_OK;
 }
 

@@ -52,7 +52,7 @@ EXPORTS = ["ns_config_default", "ns_create", "ns_batch_create", "ns_set_stream",
            "ns_profile", "ns_result",
            "ns_result_run", "ns_samples", "ns_grad_logz", "ns_state_save", "ns_state_load", "ns_last_error",
            "ns_destroy", "ns_philox", "ns_lik_forward", "ns_lik_backward", "ns_hss", "ns_knn_components",
-           "ns_sort_logl", "ns_stats_update", "ns_knn_components_noalloc"]
+           "ns_sort_logl", "ns_stats_update", "ns_knn_components_noalloc", "ns_set_means"]
 
 _lib = None
 _lock = threading.Lock()
@@ -100,6 +100,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
         L.ns_philox.argtypes = [_vp, C.c_uint32, C.c_uint32, _vp, C.c_long, _vp]
         L.ns_lik_forward.argtypes = [_vp, _vp, C.c_long, _vp, _vp, _vp]
         L.ns_lik_backward.argtypes = [_vp, _vp, C.c_long, _vp, _vp, _vp, _vp]
+        L.ns_set_means.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
         L.ns_hss.argtypes = [_vp, _vp, _vp, C.c_long, C.c_float, C.c_double, C.c_uint32, _vp, _vp, _vp,
                              C.POINTER(C.c_long), _vp]
         L.ns_knn_components.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int), _vp]
@@ -218,10 +219,10 @@ class Sampler:
         _check(load().ns_restart(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF), self.h)
 
     def profile(self, reset: bool = False) -> dict:
-        out = (C.c_double * 7)()
+        out = (C.c_double * 8)()
         _check(load().ns_profile(self.h, out, int(reset)), self.h)
         return dict(hss_ms=out[0], hss_iters=int(out[1]), launches=int(out[2]), replays=int(out[3]),
-                    hss_ms_sum=out[4], rec_overflows=int(out[5]), rec_len=int(out[6]))
+                    hss_ms_sum=out[4], rec_overflows=int(out[5]), rec_len=int(out[6]), noise_steps=int(out[7]))
 
     def result(self, run: int = 0, check: bool = True) -> dict:
         r = Result()
@@ -259,6 +260,11 @@ class Sampler:
     # ---- component calls (device pointers as ints)
     def lik_forward(self, x_ptr, n, logl_ptr, grad_ptr=None, stream=None):
         _check(load().ns_lik_forward(self.h, _vp(x_ptr), int(n), _vp(logl_ptr), _vp(grad_ptr), _vp(stream)), self.h)
+
+    def set_means(self, means, run: int = 0):
+        """Replace the component means of run `run` (n_comp x d, FP64 copy taken)."""
+        m = np.ascontiguousarray(np.asarray(means, dtype=np.float64))
+        _check(load().ns_set_means(self.h, int(run), _dp(m)), self.h)
 
     def lik_backward(self, x_ptr, n, gout_ptr, gx_ptr=None, gmu_ptr=None, stream=None):
         _check(load().ns_lik_backward(self.h, _vp(x_ptr), int(n), _vp(gout_ptr), _vp(gx_ptr), _vp(gmu_ptr),

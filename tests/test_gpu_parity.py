@@ -4,6 +4,7 @@ Integer work (Philox words, orderings, cluster labels) must match bit for bit;
 FP32 arithmetic within the tolerances stated per test; full runs statistically.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -353,3 +354,111 @@ def test_single_pass_runs_equal_three_phase_runs(monkeypatch):
         for (xa, la), (xb, lb) in zip(smp, ref_smp):
             np.testing.assert_array_equal(xa, xb)
             np.testing.assert_array_equal(la, lb)
+
+
+# ---------------------------------------------------------------- autograd.Function
+def test_autograd_gradient_is_the_walker_gradient():
+    """The d=32 four-component mixture: the x-gradient that autograd obtains through the
+    hand-written adjoint is the fused score the walkers reflect on, bit for bit; the
+    means gradient matches the oracle's analytic d log L / d mu to 1e-4."""
+    from paper_2312_03911_gb300.autograd import log_likelihood
+    w = W.workload("c2")
+    s = ggns.Sampler([w])
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(31)
+    n, d = 500, 32
+    mu = np.asarray(w["spec"]["means"])
+    x = (mu[rng.integers(0, 4, n)] + 0.04 * rng.standard_normal((n, d))).astype(np.float32)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    mt = torch.tensor(mu, dtype=torch.float32, device="cuda", requires_grad=True)
+    ll = log_likelihood(xt, mt, s)
+    ll.sum().backward()
+    logl = torch.empty(n, device="cuda")
+    grad = torch.empty((n, d), device="cuda")
+    xd = xt.detach().contiguous()
+    s.lik_forward(xd.data_ptr(), n, logl.data_ptr(), grad.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(ll.detach(), logl)
+    assert torch.equal(xt.grad, grad)
+    ref_mu = sum(lik.dmeans(x[i].astype(np.float64)) for i in range(n))
+    assert np.linalg.norm(mt.grad.cpu().numpy() - ref_mu) <= 1e-4 * max(1.0, np.linalg.norm(ref_mu))
+
+
+@pytest.mark.parametrize("kind,d", [("mix", 8), ("iso", 6), ("dense", 10), ("dense_mix", 7)])
+def test_autograd_new_means_match_oracle(kind, d):
+    """Means passed to the Function replace the context's (ns_set_means): log L, the x- and
+    mu-gradients match the oracle built with the new means."""
+    from paper_2312_03911_gb300.autograd import log_likelihood
+    w = W.small_workload(kind, d, 40, seed=40 + d)
+    s = ggns.Sampler([w])
+    rng = np.random.default_rng(7)
+    new_mu = np.asarray(w["spec"]["means"]) + 0.05 * rng.standard_normal(np.shape(w["spec"]["means"]))
+    lik = oracle.Likelihood.from_spec(dict(w["spec"], means=new_mu))
+    n = 48
+    x = (new_mu[0] + rng.uniform(-0.2, 0.2, (n, d))).astype(np.float32)
+    go = rng.normal(size=n)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    mt = torch.tensor(new_mu, dtype=torch.float32, device="cuda", requires_grad=True)
+    ll = log_likelihood(xt, mt, s)
+    (ll * torch.tensor(go, dtype=torch.float32, device="cuda")).sum().backward()
+    ref_ll = np.array([lik.loglik(v.astype(np.float64)) for v in x])
+    np.testing.assert_allclose(ll.detach().cpu().numpy(), ref_ll, rtol=1e-5, atol=1e-4)
+    ref_x = np.stack([go[i] * lik.loglik(x[i].astype(np.float64), grad=True)[1] for i in range(n)])
+    ref_mu = sum(go[i] * lik.dmeans(x[i].astype(np.float64)) for i in range(n))
+    assert np.linalg.norm(xt.grad.cpu().numpy() - ref_x) <= 1e-4 * max(1.0, np.linalg.norm(ref_x))
+    assert np.linalg.norm(mt.grad.cpu().numpy() - ref_mu) <= 1e-4 * max(1.0, np.linalg.norm(ref_mu))
+
+
+# ---------------------------------------------------------------- full-size statistics
+def _oracle_runs(w, run_ids):
+    from concurrent.futures import ThreadPoolExecutor
+    lik = oracle.Likelihood.from_spec(w["spec"])
+
+    def one(r):
+        return oracle.run(lik, w["lo"], w["hi"], oracle.make_cfg(**dict(w["cfg"], run_id=r)))
+
+    with ThreadPoolExecutor(max_workers=min(len(run_ids), os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, run_ids))
+
+
+def _posterior_moments(x, lp):
+    p = np.exp(lp - lp.max())
+    p /= p.sum()
+    m = p @ x
+    v = p @ (x - m) ** 2
+    return m, v
+
+
+def test_c2_batch_matches_oracle_statistically():
+    """The benchmark configuration (d=32 mixture, n_live 1000, clustering on), 8 replicas
+    in one batch: mean log Z within max(0.2, 3 sigma) of 8 oracle runs, and the pooled
+    posterior means and variances within 3.5 standard errors of the oracle's."""
+    w = W.workload("c2")
+    R = 8
+    runs = [dict(w, cfg=dict(w["cfg"], run_id=r)) for r in range(R)]
+    s, res = _run_gpu(runs)
+    assert all(r["status"] == 0 and r["terminated"] == 1 for r in res)
+    zg = np.array([r["logz"] for r in res])
+    orc = _oracle_runs(w, list(range(100, 100 + R)))
+    zo = np.array([o["logz"] for o in orc])
+    se = math.sqrt(zg.var(ddof=1) / R + zo.var(ddof=1) / R)
+    assert abs(zg.mean() - zo.mean()) < max(0.2, 3 * se), (zg.mean(), zo.mean(), se)
+    mg = np.array([_posterior_moments(*s.samples(r)) for r in range(R)])  # [R][2][d]
+    mo = np.array([_posterior_moments(o["dead_x"], o["dead_logw"] + o["dead_logl"]) for o in orc])
+    for q in range(2):
+        a, b = mg[:, q], mo[:, q]
+        se_q = np.sqrt(a.var(axis=0, ddof=1) / R + b.var(axis=0, ddof=1) / R) + 1e-12
+        assert np.all(np.abs(a.mean(0) - b.mean(0)) < 3.5 * se_q + 1e-6), q
+
+
+def test_c1_posterior_moments_against_closed_form():
+    """d=2 Gaussian (sigma 0.1) in [-1,1]^2: posterior mean 0 and variance 0.01 per axis
+    (the box truncation is beyond 10 sigma) within 3 standard errors over 16 replicas."""
+    w = W.workload("c1")
+    R = 16
+    s, res = _run_gpu([dict(w, cfg=dict(w["cfg"], run_id=r)) for r in range(R)])
+    mom = np.array([_posterior_moments(*s.samples(r)) for r in range(R)])
+    for q, truth in ((0, 0.0), (1, 0.01)):
+        a = mom[:, q]
+        se_q = a.std(axis=0, ddof=1) / math.sqrt(R)
+        assert np.all(np.abs(a.mean(0) - truth) < 3 * se_q + 1e-9), (q, a.mean(0), se_q)
