@@ -137,7 +137,7 @@ ns_status ns_run(ns_ctx *ctx, long max_iters);
  * Used to repeat a workload without allocating.  Synchronises. */
 ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
 
-/* Profiling counters of ctx (out[8]): out[0] milliseconds during which at
+/* Profiling counters of ctx (out[9]): out[0] milliseconds during which at
  * least one HSS kernel of ns_run was executing (union over the run groups of
  * the intervals between CUDA events recorded around the HSS kernels of each
  * iteration), out[1] group-iterations measured, out[2] kernels launched by
@@ -145,7 +145,9 @@ ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
  * intervals, out[5] iterations (summed over runs, since the last restart) whose
  * single-pass HSS ran out of step records and was redone in three phases,
  * out[6] step records per walker (0: the three-phase form only), out[7] steps
- * of momentum noise drawn ahead per walker (0: drawn during the walk).
+ * of momentum noise drawn ahead per walker (0: drawn during the walk), out[8]
+ * walker classes stepping CTA-cooperatively (dense likelihoods whose precision
+ * matrix is read from global memory in shared tiles).
  * reset != 0 zeroes out[0..4] after reading.  Synchronises. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 

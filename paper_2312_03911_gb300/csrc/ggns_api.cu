@@ -62,6 +62,9 @@ struct RunClass {
     int prec_in_smem = 0;
     int single = 0;    // HSS in one pass (every walker block resident at once)
     int fallback = 1;  // three-phase kernels after the single pass (records shorter than n_steps)
+    int coop = 0;      // dense kinds with P outside shared memory: the CTA-cooperative single pass
+    int coop_tr = 0;   // rows of P per shared-memory tile
+    size_t coop_smem = 0;
 };
 
 // Runs advanced together by one CUDA graph on one stream.  Different groups
@@ -406,8 +409,12 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
     // three phases (for single-pass classes only if the records overflowed)
     for (auto &cl : g.classes)
         if (cl.single) {
-            CU(kind_launch(cl.kind).hss1(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
-                                         ctx->rec_base_dev, cl.smem, cl.prec_in_smem, s));
+            if (cl.coop)
+                CU(kind_launch(cl.kind).hss1_coop(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
+                                                  ctx->rec_base_dev, cl.coop_smem, cl.coop_tr, s));
+            else
+                CU(kind_launch(cl.kind).hss1(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec,
+                                             ctx->rec_base_dev, cl.smem, cl.prec_in_smem, s));
             ++n;
         }
     for (auto &cl : g.classes)
@@ -797,6 +804,40 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                         rc.single = blocks <= (long)per_sm * n_sm ? 1 : 0;
                         rc.fallback = 0;
                         for (int r : rc.runs) rc.fallback |= (ctx->rec.rec_len < cfg[r].n_steps);
+                        // dense likelihoods whose P stays in global memory: walkers of a CTA share each
+                        // tile of P (GGNS_COOP=0 keeps one read of P per walker-step)
+                        const char *cv = getenv("GGNS_COOP");
+                        const bool want = !(cv && atoi(cv) == 0);
+                        const bool dense = rc.kind == NS_LIK_DENSE_GAUSS || rc.kind == NS_LIK_DENSE_MIX;
+                        if (want && dense && !rc.prec_in_smem && !rc.fallback &&
+                            (rc.tile == 6 || rc.tile == 7 || rc.tile == 8)) {
+                            size_t par = 0;
+                            int dpm = 0;
+                            bool aligned = true;
+                            for (int r : rc.runs) {
+                                const RunDesc &Dr = ctx->desc[r];
+                                par = std::max(par, (size_t)param_smem_floats(Dr, false));
+                                dpm = std::max(dpm, Dr.d_pad);
+                                const ParLayout Lr = par_layout(Dr.d, Dr.d_pad, Dr.n_comp, Dr.kind);
+                                aligned &= ((Dr.par_off + Lr.prec) % 4) == 0;
+                            }
+                            const size_t base = 4 * (par + (size_t)(COOP_THREADS / 32) * dpm) + 16;
+                            for (int tr = 64; tr >= 8 && aligned; tr /= 2) {
+                                const size_t need = base + 2 * 4 * (size_t)tr * dpm;
+                                if (need > SMEM_LIMIT) continue;
+                                int cps = 0;
+                                CU(kind_launch(rc.kind).hss1_coop_occ(rc.tile, need, &cps));
+                                const long cb = (rc.max_k + COOP_THREADS / 32 - 1) / (COOP_THREADS / 32) *
+                                                (long)rc.runs.size();
+                                if (cps > 0 && cb <= (long)cps * n_sm) {
+                                    rc.coop = 1;
+                                    rc.coop_tr = tr;
+                                    rc.coop_smem = need;
+                                    rc.single = 1;
+                                }
+                                break;
+                            }
+                        }
                     }
                 }
                 CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
@@ -1007,6 +1048,10 @@ ns_status ns_profile(const ns_ctx *cctx, double *out, int reset)
     out[5] = (double)over;
     out[6] = ctx->rec.rec_len;
     out[7] = ctx->rec.nT;
+    int ncoop = 0;
+    for (auto &g : ctx->groups)
+        for (auto &cl : g.classes) ncoop += cl.coop;
+    out[8] = ncoop;
     if (reset) {
         ctx->hss_ms = ctx->hss_ms_sum = 0.0;
         ctx->hss_iters = ctx->launches = ctx->replays = 0;

@@ -7,7 +7,8 @@ namespace ggns {
 const KindLaunch &kind_launch_dense()
 {
     static const KindLaunch L{kind_dense::prior, kind_dense::hss, kind_dense::lik, kind_dense::grad, kind_dense::smem_attr, kind_dense::hss1,
-                                kind_dense::hss1_occ};
+                                kind_dense::hss1_occ, kind_dense::hss1_coop,
+                                kind_dense::hss1_coop_occ};
     return L;
 }
 }  // namespace ggns

@@ -112,6 +112,61 @@ __device__ __forceinline__ float lik_mix_slots(const ParView &P, int dp, const f
     return m + __logf(s);
 }
 
+// Dense kinds after y = P v (v = x - mu, or x for the mixture): the quadratic
+// forms, the log-sum-exp over the components and the score.
+template <int KIND, int G, int E>
+__device__ __forceinline__ float dense_finish(const RunDesc &D, const ParView &P, const float (&x)[E],
+                                              const float (&y)[E], float (&g)[E], int c0, float *dmu_w)
+{
+    const int dp = D.d_pad;
+    const bool mix = (KIND == NS_LIK_DENSE_MIX);
+    const int K = mix ? D.n_comp : 1;
+    if (!mix) {
+        float q = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float r = x[e] - P.means[c0 + e];
+            q = fmaf(r, y[e], q);
+            g[e] = -y[e];
+        }
+        q = gsum<G>(q);
+        if (dmu_w) dmu_w[0] = 1.f;
+        return D.lik_const - 0.5f * q;
+    }
+    float m = -INFINITY, s = 0.f;
+    float acc[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        const float *mu = P.means + (long)k * dp + c0;
+        const float *pm = P.pmu + (long)k * dp + c0;
+        float q = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
+        q = gsum<G>(q);
+        const float tk = P.b[k] - 0.5f * q;
+        if (tk > m) {
+            const float sc = (m == -INFINITY) ? 0.f : expf(m - tk);
+            s *= sc;
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] *= sc;
+            m = tk;
+        }
+        const float wk = expf(tk - m);
+        s += wk;
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, y[e] - pm[e], acc[e]);
+        if (dmu_w) dmu_w[k] = tk;
+    }
+    const float inv = 1.f / s;
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+    if (dmu_w) {
+        for (int k = 0; k < K; ++k) dmu_w[k] = expf(dmu_w[k] - m) * inv;
+    }
+    return D.lik_const + m + logf(s);
+}
+
 template <int KIND, int G, int E>
 __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E],
                                           int c0, float *rbuf, float *dmu_w)
@@ -225,7 +280,6 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
     } else {
         // dense kinds: y = P v on CUDA cores, v staged through the walker's shared buffer
         const bool mix = (KIND == NS_LIK_DENSE_MIX);
-        const int K = mix ? D.n_comp : 1;
         // stage v = x - mu (single Gaussian) or x (mixture: P x, then subtract P mu_k)
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -245,51 +299,70 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
             for (int e = 0; e < E; ++e) y[e] = fmaf(row[e], vj, y[e]);
         }
         __syncwarp();
-        if (!mix) {
-            float q = 0.f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float r = x[e] - P.means[c0 + e];
-                q = fmaf(r, y[e], q);
-                g[e] = -y[e];
-            }
-            q = gsum<G>(q);
-            if (dmu_w) dmu_w[0] = 1.f;
-            return D.lik_const - 0.5f * q;
-        }
-        float m = -INFINITY, s = 0.f;
-        float acc[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = 0.f;
-        for (int k = 0; k < K; ++k) {
-            const float *mu = P.means + (long)k * dp + c0;
-            const float *pm = P.pmu + (long)k * dp + c0;
-            float q = 0.f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
-            q = gsum<G>(q);
-            const float tk = P.b[k] - 0.5f * q;
-            if (tk > m) {
-                const float sc = (m == -INFINITY) ? 0.f : expf(m - tk);
-                s *= sc;
-#pragma unroll
-                for (int e = 0; e < E; ++e) acc[e] *= sc;
-                m = tk;
-            }
-            const float wk = expf(tk - m);
-            s += wk;
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, y[e] - pm[e], acc[e]);
-            if (dmu_w) dmu_w[k] = tk;
-        }
-        const float inv = 1.f / s;
-#pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
-        if (dmu_w) {
-            for (int k = 0; k < K; ++k) dmu_w[k] = expf(dmu_w[k] - m) * inv;
-        }
-        return D.lik_const + m + logf(s);
+        return dense_finish<KIND, G, E>(D, P, x, y, g, c0, dmu_w);
     }
+}
+
+// Dense likelihood of every walker of a CTA at once (one walker per warp, G = 32):
+// the CTA streams the precision matrix through shared memory in tiles of `tr`
+// rows (cp.async, double-buffered), so one read of P serves all its walkers
+// instead of one per walker.  Each lane accumulates y = P v over the rows in the
+// same order as lik_eval, so the result is the same to the bit.  Every thread of
+// the CTA calls it (barriers inside); ptile holds 2 * tr * d_pad floats.
+__device__ __forceinline__ void cp_async16(float *dst_smem, const float *src_gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src_gmem) : "memory");
+}
+
+template <int KIND, int E>
+__device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
+                                float *rbuf, float *ptile, int tr)
+{
+    const int d = D.d, dp = D.d_pad;
+    const bool mix = (KIND == NS_LIK_DENSE_MIX);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = c0 + e;
+        float v = 0.f;
+        if (c < d) v = mix ? x[e] : x[e] - P.means[c];
+        rbuf[c] = v;
+    }
+    float y[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = 0.f;
+    const int ntiles = (d + tr - 1) / tr;
+    const int chunks_per_row = dp >> 2;
+    auto load_tile = [&](int t, float *buf) {
+        const int j0 = t * tr, jn = min(tr, d - j0);
+        const int n = jn * chunks_per_row;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int jj = i / chunks_per_row, q = i - jj * chunks_per_row;
+            cp_async16(buf + jj * dp + 4 * q, P.prec + (long)(j0 + jj) * dp + 4 * q);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    __syncthreads();  // every walker has staged v; the tiles of the previous call are no longer read
+    load_tile(0, ptile);
+    for (int t = 0; t < ntiles; ++t) {
+        if (t + 1 < ntiles) {
+            load_tile(t + 1, ptile + ((t + 1) & 1) * tr * dp);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const float *tb = ptile + (t & 1) * tr * dp;
+        const int j0 = t * tr, jn = min(tr, d - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const float vj = rbuf[j0 + jj];
+            const float *row = tb + jj * dp + c0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = fmaf(row[e], vj, y[e]);
+        }
+        __syncthreads();  // the buffer of tile t is refilled by the load of tile t + 2
+    }
+    return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
 }
 
 // ------------------------------------------------------------------------
@@ -605,10 +678,18 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 // x[(w * rec_len + t - 1) * xs + c] (inside steps only), rows offset by the run's rec_base.
 // ------------------------------------------------------------------------
 
-template <int KIND, int G, int E>
-__global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx C, const int *run_list, RecView R,
-                                                                         const long *rec_base, int prec_in_smem)
+// COOP: dense kinds whose precision matrix does not fit in shared memory; one
+// walker per warp, COOP_THREADS / 32 walkers per CTA stepping together, each CTA
+// taking a fixed block of walkers, the likelihood from lik_dense_coop with P
+// tiles of coop_tr rows.  Same trajectories as the form with one walker group
+// per refill.
+constexpr int COOP_THREADS = 512;
+
+template <int KIND, int G, int E, bool COOP = false>
+__global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : ((E >= 16) ? 2 : 4))
+    k_hss1(DevCtx C, const int *run_list, RecView R, const long *rec_base, int prec_in_smem, int coop_tr)
 {
+    static_assert(!COOP || G == 32, "one walker per warp");
     extern __shared__ float smem[];
     const int r = run_list[blockIdx.y];
     const RunDesc D = C.desc[r];
@@ -630,6 +711,15 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
     const int W = D.k;
     const int dp = D.d_pad;
     const int L = min(R.rec_len, D.n_steps);
+    // COOP: the P tiles follow the walkers' buffers (16-byte aligned)
+    float *ptile = nullptr;
+    if constexpr (COOP) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(rbase + (long)(blockDim.x / 32) * dp);
+        ptile = reinterpret_cast<float *>((a + 15) & ~uintptr_t(15));
+    }
+    bool coop_first = true;
+    (void)coop_first;
+    (void)coop_tr;
     const uint32_t iter = static_cast<uint32_t>(S->iter);
     const float dt = static_cast<float>(S->dt);
     const float lstar = static_cast<float>(S->lstar);
@@ -657,8 +747,14 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
     for (;;) {
         if (!active && !exhausted) {
             unsigned wid = 0;
-            if (lig == 0) wid = atomicAdd(&S->wcount1, 1u);
-            wid = __shfl_sync(gmask, wid, gbase);
+            if constexpr (COOP) {
+                // a fixed walker per warp, taken once
+                wid = coop_first ? static_cast<unsigned>(blockIdx.x * (blockDim.x / 32) + grp) : static_cast<unsigned>(W);
+                coop_first = false;
+            } else {
+                if (lig == 0) wid = atomicAdd(&S->wcount1, 1u);
+                wid = __shfl_sync(gmask, wid, gbase);
+            }
             if (wid >= static_cast<unsigned>(W)) {
                 exhausted = true;
             } else {
@@ -722,7 +818,11 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
             }
             if (at_stop || t >= L) active = false;
         }
-        if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        if constexpr (COOP) {
+            if (!__syncthreads_or(active)) break;
+        } else {
+            if (!__any_sync(0xffffffffu, active || !exhausted)) break;
+        }
         const bool stepping = active;
         // the registration count for the next stop test, read while this step runs
         if (stepping && reg_max && rem_seen != 0) rem_seen = *v_remain;
@@ -745,7 +845,12 @@ __global__ void __launch_bounds__(HSS_THREADS, (E >= 16) ? 2 : 4) k_hss1(DevCtx 
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
-        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        float ll;
+        if constexpr (COOP) {
+            ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
+        } else {
+            ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        }
         int outbox = 0;
         float nb[E];
 #pragma unroll

@@ -52,7 +52,7 @@ static cudaError_t hss1_t(const DevCtx &C, const int *runs, int nr, int max_k, c
 {
     const int gpc = HSS_THREADS / G;
     const int bx = (max_k + gpc - 1) / gpc;
-    k_hss1<KIND, G, E><<<dim3(bx, nr), HSS_THREADS, smem, s>>>(C, runs, R, rec_base, pis);
+    k_hss1<KIND, G, E><<<dim3(bx, nr), HSS_THREADS, smem, s>>>(C, runs, R, rec_base, pis, 0);
     return cudaGetLastError();
 }
 template <int G, int E>
@@ -125,6 +125,50 @@ static cudaError_t hss1(int tile, const DevCtx &C, const int *runs, int nr, int 
 static cudaError_t hss1_occ(int tile, size_t smem, int *blocks_per_sm)
 {
     GGNS_DISPATCH(occ_t, smem, blocks_per_sm)
+}
+
+// The CTA-cooperative single pass (dense kinds, one walker per warp): tiles 6, 7, 8.
+template <int E>
+static cudaError_t coop_t(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
+                          size_t smem, int tr, cudaStream_t s)
+{
+    const int wpc = COOP_THREADS / 32;
+    const int bx = (max_k + wpc - 1) / wpc;
+    k_hss1<KIND, 32, E, true><<<dim3(bx, nr), COOP_THREADS, smem, s>>>(C, runs, R, rec_base, 0, tr);
+    return cudaGetLastError();
+}
+template <int E>
+static cudaError_t coop_occ_t(size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_hss1<KIND, 32, E, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, 32, E, true>, COOP_THREADS, smem);
+}
+template <int KD>
+static cudaError_t coop_dispatch(int tile, bool occ, const DevCtx *C, const int *runs, int nr, int max_k,
+                                 const RecView *R, const long *rec_base, size_t smem, int tr, int *blocks_per_sm,
+                                 cudaStream_t s)
+{
+    if constexpr (KD == NS_LIK_DENSE_GAUSS || KD == NS_LIK_DENSE_MIX) {
+        switch (tile) {
+        case 6: return occ ? coop_occ_t<4>(smem, blocks_per_sm) : coop_t<4>(*C, runs, nr, max_k, *R, rec_base, smem, tr, s);
+        case 7: return occ ? coop_occ_t<8>(smem, blocks_per_sm) : coop_t<8>(*C, runs, nr, max_k, *R, rec_base, smem, tr, s);
+        case 8: return occ ? coop_occ_t<16>(smem, blocks_per_sm) : coop_t<16>(*C, runs, nr, max_k, *R, rec_base, smem, tr, s);
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+static cudaError_t hss1_coop(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
+                             const long *rec_base, size_t smem, int tr, cudaStream_t s)
+{
+    return coop_dispatch<KIND>(tile, false, &C, runs, nr, max_k, &R, rec_base, smem, tr, nullptr, s);
+}
+static cudaError_t hss1_coop_occ(int tile, size_t smem, int *blocks_per_sm)
+{
+    return coop_dispatch<KIND>(tile, true, nullptr, nullptr, 0, 0, nullptr, nullptr, smem, 0, blocks_per_sm, nullptr);
 }
 
 }  // namespace GGNS_KIND_NS

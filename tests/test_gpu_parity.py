@@ -462,3 +462,20 @@ def test_c1_posterior_moments_against_closed_form():
         a = mom[:, q]
         se_q = a.std(axis=0, ddof=1) / math.sqrt(R)
         assert np.all(np.abs(a.mean(0) - truth) < 3 * se_q + 1e-9), (q, a.mean(0), se_q)
+
+
+def test_cooperative_dense_walk_equals_per_walker_walk(monkeypatch):
+    """d=256 dense mixture (P does not fit in shared memory): the walk in which the walkers of a
+    CTA share each tile of P gives the same runs, bit for bit, as one read of P per walker."""
+    w = W.small_workload("dense_mix", 256, 160, seed=61)
+    w = dict(w, cfg=dict(w["cfg"], n_steps=120, max_iters=12))
+    out = {}
+    for coop in (0, 1):
+        monkeypatch.setenv("GGNS_COOP", str(coop))
+        s = ggns.Sampler([w])
+        s.step(12)
+        out[coop] = (s.result(0, check=False), s.profile()["coop_classes"])
+    assert out[0][1] == 0 and out[1][1] == 1
+    a, b = out[0][0], out[1][0]
+    for key in ("logz", "logz_err", "n_like", "dt", "n_iter", "n_dead"):
+        assert a[key] == b[key], key
