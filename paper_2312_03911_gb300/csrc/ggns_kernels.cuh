@@ -319,6 +319,11 @@ template <int KIND, int E>
 __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
                                 float *rbuf, float *ptile, int tr)
 {
+    // Y[16][d_pad] = V[16][d] P as a register-blocked product: thread (wg, cg) accumulates
+    // walkers 4 wg .. 4 wg + 3 by columns NC cg .. NC cg + NC - 1 (NC = d_pad / 128), so each
+    // element of a P tile is read from shared memory by 4 threads instead of 16 warps.
+    constexpr int NC = (E * 32) / 128;
+    static_assert(NC >= 1 && NC * 128 == E * 32, "d_pad a multiple of 128");
     const int d = D.d, dp = D.d_pad;
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
 #pragma unroll
@@ -328,9 +333,6 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
         if (c < d) v = mix ? x[e] : x[e] - P.means[c];
         rbuf[c] = v;
     }
-    float y[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = 0.f;
     const int ntiles = (d + tr - 1) / tr;
     const int chunks_per_row = dp >> 2;
     auto load_tile = [&](int t, float *buf) {
@@ -342,6 +344,13 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
+    const int wg = threadIdx.x >> 7, cg = threadIdx.x & 127;
+    const float *vrow = rbuf - (long)(threadIdx.x >> 5) * dp + (long)(4 * wg) * dp;  // V row of walker 4 wg
+    float acc[4][NC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[i][c] = 0.f;
     __syncthreads();  // every walker has staged v; the tiles of the previous call are no longer read
     load_tile(0, ptile);
     for (int t = 0; t < ntiles; ++t) {
@@ -352,16 +361,31 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
-        const float *tb = ptile + (t & 1) * tr * dp;
+        const float *tb = ptile + (t & 1) * tr * dp + NC * cg;
         const int j0 = t * tr, jn = min(tr, d - j0);
         for (int jj = 0; jj < jn; ++jj) {
-            const float vj = rbuf[j0 + jj];
-            const float *row = tb + jj * dp + c0;
+            float pv[NC];
 #pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = fmaf(row[e], vj, y[e]);
+            for (int c = 0; c < NC; ++c) pv[c] = tb[jj * dp + c];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float vj = vrow[(long)i * dp + j0 + jj];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[i][c] = fmaf(pv[c], vj, acc[i][c]);
+            }
         }
         __syncthreads();  // the buffer of tile t is refilled by the load of tile t + 2
     }
+    // Y through the tile buffer (16 x d_pad floats fit in 2 tr d_pad), then each walker reads its columns
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ptile[(long)(4 * wg + i) * dp + NC * cg + c] = acc[i][c];
+    __syncthreads();
+    float y[E];
+    const float *yrow = ptile + (long)(threadIdx.x >> 5) * dp + c0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) y[e] = yrow[e];
     return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
 }
 
