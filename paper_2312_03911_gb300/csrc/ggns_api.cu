@@ -51,6 +51,7 @@ namespace {
 
 constexpr int GRAPH_ITERS = 8;
 constexpr size_t SMEM_LIMIT = 200 * 1024;
+constexpr size_t COOP_SMEM_LIMIT = 227 * 1024;  // one CTA per SM: the whole opt-in shared memory
 constexpr int NOISE_BLOCKS_PER_RUN = 64;
 
 struct RunClass {
@@ -824,7 +825,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                             const size_t base = 4 * (par + (size_t)(COOP_THREADS / 32) * dpm) + 16;
                             for (int tr = 64; tr >= 8 && aligned; tr /= 2) {
                                 const size_t need = base + 2 * 4 * (size_t)tr * dpm;
-                                if (need > SMEM_LIMIT) continue;
+                                if (need > COOP_SMEM_LIMIT) continue;
                                 int cps = 0;
                                 CU(kind_launch(rc.kind).hss1_coop_occ(rc.tile, need, &cps));
                                 const long cb = (rc.max_k + COOP_THREADS / 32 - 1) / (COOP_THREADS / 32) *

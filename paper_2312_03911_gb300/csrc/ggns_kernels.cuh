@@ -315,6 +315,35 @@ __device__ __forceinline__ void cp_async16(float *dst_smem, const float *src_gme
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src_gmem) : "memory");
 }
 
+// NC consecutive floats at a 4 NC-byte aligned shared address, in one access
+// (NC = 1, 2, 4): a warp then reads 32 NC consecutive floats without bank conflicts.
+template <int NC>
+__device__ __forceinline__ void vec_load(const float *p, float (&v)[NC])
+{
+    if constexpr (NC == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (NC == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x; v[1] = q.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c] = p[c];
+    }
+}
+template <int NC>
+__device__ __forceinline__ void vec_store(float *p, const float (&v)[NC])
+{
+    if constexpr (NC == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (NC == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) p[c] = v[c];
+    }
+}
+
 template <int KIND, int E>
 __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
                                 float *rbuf, float *ptile, int tr)
@@ -365,8 +394,7 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
         const int j0 = t * tr, jn = min(tr, d - j0);
         for (int jj = 0; jj < jn; ++jj) {
             float pv[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) pv[c] = tb[jj * dp + c];
+            vec_load<NC>(tb + jj * dp, pv);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float vj = vrow[(long)i * dp + j0 + jj];
@@ -378,9 +406,7 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
     }
     // Y through the tile buffer (16 x d_pad floats fit in 2 tr d_pad), then each walker reads its columns
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ptile[(long)(4 * wg + i) * dp + NC * cg + c] = acc[i][c];
+    for (int i = 0; i < 4; ++i) vec_store<NC>(ptile + (long)(4 * wg + i) * dp + NC * cg, acc[i]);
     __syncthreads();
     float y[E];
     const float *yrow = ptile + (long)(threadIdx.x >> 5) * dp + c0;
