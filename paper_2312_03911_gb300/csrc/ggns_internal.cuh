@@ -41,11 +41,13 @@ struct RecView {
 };
 
 // Steps of noise drawn ahead for an iteration: all nT for the first iteration,
-// then 1.5 x the previous t_stop + 16 (at most nT); later steps draw inline.
+// then 1.1 x the previous t_stop + 4 (at most nT); later steps draw inline.  The
+// draw competes with the k-NN for the SMs, so a tight estimate pays (t_stop moves
+// little between iterations).
 __host__ __device__ inline int noise_steps(int nT, int t_stop_last)
 {
     if (t_stop_last <= 0) return nT;
-    const int n = t_stop_last + t_stop_last / 2 + 16;
+    const int n = t_stop_last + t_stop_last / 10 + 4;
     return n < nT ? n : nT;
 }
 

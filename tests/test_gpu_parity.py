@@ -525,3 +525,35 @@ def test_c5_full_size_run():
     _sampled_logl_check(s, w)
     g = s.grad_logz(0)
     assert np.all(np.isfinite(g))
+
+
+# ---------------------------------------------------------------- autotuned uneven batch
+def test_c4_batch_with_autotuned_tiles(monkeypatch):
+    """The 64 uneven runs (d 8..256, n_live 100..1000, three likelihood kinds) in one context
+    with tiles chosen by the autotuner: every run terminates, and every run with d <= 16 and
+    n_live <= 250 (all three kinds) agrees with the oracle run of the same configuration within
+    max(0.3, 4 sigma) of their combined error estimates."""
+    from paper_2312_03911_gb300 import autotune
+    runs = W.batched_runs()
+    choice = autotune.autotune(runs)
+    for (kind, d), tile in choice.items():
+        g, e = autotune.TILES[tile]
+        assert d <= g * e <= 2 * max(d, 2)
+        monkeypatch.setenv(autotune.env_name(kind, d), str(tile))
+    s, res = _run_gpu(runs)
+    assert all(r["status"] == 0 and r["terminated"] == 1 for r in res)
+    small = [i for i, w in enumerate(runs) if w["spec"]["d"] <= 16 and w["cfg"]["n_live"] <= 250]
+    assert len(small) >= 10
+    from concurrent.futures import ThreadPoolExecutor
+
+    def orc(i):
+        w = runs[i]
+        lik = oracle.Likelihood.from_spec(w["spec"])
+        return oracle.run(lik, w["lo"], w["hi"], oracle.make_cfg(**w["cfg"]))
+
+    with ThreadPoolExecutor(max_workers=min(len(small), os.cpu_count() or 1)) as ex:
+        orcs = list(ex.map(orc, small))
+    for i, o in zip(small, orcs):
+        r = res[i]
+        tol = max(0.3, 4 * math.sqrt(r["logz_err"] ** 2 + o["logz_err"] ** 2))
+        assert abs(r["logz"] - o["logz"]) < tol, (runs[i]["name"], r["logz"], o["logz"], tol)
