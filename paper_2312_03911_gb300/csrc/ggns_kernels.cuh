@@ -909,20 +909,20 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             nb[e] = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
             outbox += (nb[e] != 0.f);
         }
-        outbox = gsum_i<G>(outbox);
-        const bool outside = (outbox > 0) || !(ll > lstar);
+        // the reflection's group sums are reduced together with the box count: four
+        // independent trees instead of two in sequence behind a vote (same sums)
         float pnb = 0.f, pg = 0.f, gg = 0.f;
-        if (__any_sync(0xffffffffu, stepping && outside)) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                pnb = fmaf(p[e], nb[e], pnb);
-                pg = fmaf(p[e], g[e], pg);
-                gg = fmaf(g[e], g[e], gg);
-            }
-            pnb = gsum<G>(pnb);
-            pg = gsum<G>(pg);
-            gg = gsum<G>(gg);
+        for (int e = 0; e < E; ++e) {
+            pnb = fmaf(p[e], nb[e], pnb);
+            pg = fmaf(p[e], g[e], pg);
+            gg = fmaf(g[e], g[e], gg);
         }
+        outbox = gsum_i<G>(outbox);
+        pnb = gsum<G>(pnb);
+        pg = gsum<G>(pg);
+        gg = gsum<G>(gg);
+        const bool outside = (outbox > 0) || !(ll > lstar);
         if (stepping && outside) {
             if (outbox > 0) {
                 const float cc = __fdividef(2.f * pnb, static_cast<float>(outbox));
