@@ -124,6 +124,26 @@ def replicas(R: int, rank: int):
     return w, [dict(w, cfg=dict(w["cfg"], run_id=rank * R + r)) for r in range(R)]
 
 
+def max_over_ranks(t: float, dist, device: str) -> float:
+    """A step ends when the slowest rank ends: the maximum of the ranks' step times."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def sum_over_ranks(x: float, dist, device: str) -> float:
+    """Whole-job totals (point-steps of every rank's replicas)."""
+    if dist is None:
+        return x
+    import torch
+    tt = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(tt)
+    return float(tt.item())
+
+
 def measured_traffic():
     """The profiled traffic per launch, or None once the kernel sources differ from the profiled ones."""
     import hashlib
@@ -264,22 +284,14 @@ def gpu_arm(args):
             res = one_step(W.SEED_BASE + 2000 + i)
             ev1.record(stream)
             torch.cuda.synchronize()
-            t = ev0.elapsed_time(ev1) / 1000.0
-            if dist is not None:
-                tt = torch.tensor([t], device="cuda")
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                t = float(tt.item())
+            t = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, dist, "cuda")
             times.append(t)
             pts.append(sum(r["n_steps_total"] for r in res))
             logz.append([r["logz"] for r in res])
             errs.append([r["logz_err"] for r in res])
     prof = s.profile(reset=True)
     clocks = clk.summary()
-    tot_pts = sum(pts)
-    if dist is not None:
-        tp = torch.tensor([float(tot_pts)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tp)
-        tot_pts = float(tp.item())
+    tot_pts = sum_over_ranks(float(sum(pts)), dist, "cuda")
     value = tot_pts / sum(times)
     ms = 1000.0 * sum(times) / len(times)
     # roofline of the dominant kernel (HSS): algorithmic lane-ops / HSS time

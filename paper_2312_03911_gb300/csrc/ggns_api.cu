@@ -387,16 +387,11 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
         CU(launch_knn(C, g.r0, g.nr, g.max_n, ctx->knn_smem, s));
         ++n;
     }
-    if (!first) {
-        ns_status ts = launch_term_join(ctx, g, s);
-        if (ts != NS_OK) return ts;
-        ++n;
-    }
-    if (ctx->any_clustering) {
-        CU(launch_cluster(C, g.r0, g.nr, ctx->lastkey, ctx->cl_smem, s));
-        ++n;
-    }
-    CU(launch_sort(C, g.r0, g.nr, ctx->sort_smem, s));
+    // the previous iteration's termination test once its statistics are in, then
+    // cluster finding and selection: one kernel per run
+    if (!first) CU(cudaStreamWaitEvent(s, g.join_ev, 0));
+    CU(launch_term_cluster_sort(C, g.r0, g.nr, ctx->lastkey, std::max(ctx->cl_smem, ctx->sort_smem), !first,
+                                ctx->any_clustering, s));
     ++n;
     // fork: the FP64 statistics of this iteration's kills beside the HSS phases
     CU(cudaEventRecord(g.fork_ev, s));

@@ -563,10 +563,8 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
 // ------------------------------------------------------------------------
 constexpr int SORT_THREADS = 1024;
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
+__device__ void sort_body(DevCtx C, int r, unsigned char *sraw)
 {
-    extern __shared__ unsigned char sraw[];
-    const int r = r0 + blockIdx.x;
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done) return;
@@ -738,6 +736,12 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
     }
 }
 
+__global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
+{
+    extern __shared__ unsigned char sraw[];
+    sort_body(C, r0 + blockIdx.x, sraw);
+}
+
 // ------------------------------------------------------------------------
 // Appendix H statistics of the iteration's kills (FP64), beside the HSS phases.
 // Reads the kills from the dead records, writes their log prior masses, applies
@@ -848,11 +852,8 @@ __global__ void k_tail(DevCtx C, int r0)
 // FP64 statistics are in, which lets them overlap the tail and the next
 // iteration's k-NN.  XL peak on the dead-point sequence (termination 0) or
 // X L_max < tol Z (termination 1); then the iteration cap.
-__global__ void k_term(DevCtx C, int r0, int n_runs)
+__device__ void term_body(DevCtx C, int r)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_runs) return;
-    const int r = r0 + t;
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done || !S->term_pending) return;
@@ -876,6 +877,12 @@ __global__ void k_term(DevCtx C, int r0, int n_runs)
         S->status = NS_ERR_NOT_DONE;
         S->done = 1;
     }
+}
+
+__global__ void k_term(DevCtx C, int r0, int n_runs)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_runs) term_body(C, r0 + t);
 }
 
 // Reservoir replay over the recorded window and emission of every walker's new
@@ -1393,10 +1400,8 @@ __device__ void stats_split(Stats *st, int p, int np, const int *sz, const int *
 
 constexpr int CL_THREADS = 1024;
 
-__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all, int r0)
+__device__ void cluster_body(DevCtx C, unsigned long long *lastkey_all, int r, int *csm)
 {
-    extern __shared__ int csm[];
-    const int r = r0 + blockIdx.x;
     const RunDesc &D = C.desc[r];
     RunState *S = C.state + r;
     if (S->done || !D.clustering) return;
@@ -1515,6 +1520,29 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long 
         S->n_clusters = na;
         if (na > S->max_clusters) S->max_clusters = na;
     }
+}
+
+__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all, int r0)
+{
+    extern __shared__ int csm[];
+    cluster_body(C, lastkey_all, r0 + blockIdx.x, csm);
+}
+
+// Termination test of the previous iteration, cluster finding and selection of this
+// one, for one run per CTA: one launch instead of three on the iteration's path.
+static_assert(CL_THREADS == SORT_THREADS, "one block shape");
+__global__ void __launch_bounds__(SORT_THREADS) k_term_cluster_sort(DevCtx C, unsigned long long *lastkey_all, int r0,
+                                                                  int do_term, int clustering)
+{
+    extern __shared__ unsigned char fsm[];
+    const int r = r0 + blockIdx.x;
+    if (do_term && threadIdx.x == 0) term_body(C, r);
+    __syncthreads();
+    if (clustering) {
+        cluster_body(C, lastkey_all, r, reinterpret_cast<int *>(fsm));
+        __syncthreads();
+    }
+    sort_body(C, r, fsm);
 }
 
 size_t cluster_smem_bytes(int n_live_max) { return sizeof(int) * 3 * (size_t)n_live_max; }
@@ -1647,9 +1675,15 @@ __global__ void k_reduce_parts(const double *part, int n_parts, int len, double 
     }
 }
 
+// Opt a kernel in to `smem` bytes of dynamic shared memory when its static and
+// dynamic shared memory together exceed the default 48 KiB.
 static cudaError_t set_max_smem(const void *fn, size_t smem)
 {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    if (smem + a.sharedSizeBytes > 48 * 1024)
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaSuccess;
 }
 
@@ -1660,6 +1694,8 @@ cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t c
     if ((e = set_max_smem((const void *)k_evidence, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_final, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_knn, knn_smem)) != cudaSuccess) return e;
+    if ((e = set_max_smem((const void *)k_term_cluster_sort, cl_smem > sort_smem ? cl_smem : sort_smem)) != cudaSuccess)
+        return e;
     return set_max_smem((const void *)k_cluster, cl_smem);
 }
 
@@ -1721,6 +1757,12 @@ cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k,
                             cudaStream_t s)
 {
     k_hss_pick<<<dim3((max_k + PICK_WARPS - 1) / PICK_WARPS, nr), PICK_WARPS * 32, 0, s>>>(C, runs, R, rec_base);
+    return cudaGetLastError();
+}
+cudaError_t launch_term_cluster_sort(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
+                                     bool do_term, bool clustering, cudaStream_t s)
+{
+    k_term_cluster_sort<<<n_runs, SORT_THREADS, smem, s>>>(C, lastkey, r0, do_term ? 1 : 0, clustering ? 1 : 0);
     return cudaGetLastError();
 }
 cudaError_t launch_term(const DevCtx &C, int r0, int n_runs, cudaStream_t s)
