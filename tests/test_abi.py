@@ -47,3 +47,14 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     w["cfg"] = dict(n_live=100, min_ref=4, max_ref=3)
     with pytest.raises(ggns.GGNSError):
         ggns.Sampler([w])
+
+
+def test_autotune_candidates_hold_d_without_doubling_the_padding():
+    from paper_2312_03911_gb300 import autotune
+    for d in (2, 3, 8, 17, 32, 64, 100, 256, 512):
+        c = autotune.candidates(d)
+        assert c, d
+        for t in c:
+            g, e = autotune.TILES[t]
+            assert d <= g * e <= 2 * max(d, 2)
+    assert autotune.env_name(1, 32) == "GGNS_TILE_1_32"
