@@ -992,13 +992,35 @@ __device__ __forceinline__ float sqdist_rn(const float *a, const float *b, int d
     return s;
 }
 
-// Cluster sizes from the labels (every CTA counts them itself: n reads).
-__device__ void knn_label_counts(int n, const int *label, int *s_cnt /* [CMAX] */)
+constexpr int KQ_TILE = 128;
+static_assert(KQ_TILE == KQ_WARPS * 32, "one tile row per thread in the compaction");
+constexpr int KQ_MSTRIDE = KNN_K + 1;  // merge-list stride per lane (u64): spreads the banks
+
+// Labels of the points, read from a byte copy in shared memory when the run is
+// small enough (n <= KQ_LAB_CAP), else from global memory.
+constexpr int KQ_LAB_CAP = 4096;
+struct LabelView {
+    const int *g;
+    const unsigned char *s;
+    bool in_smem;
+    __device__ __forceinline__ int operator()(int j) const { return in_smem ? (int)s[j] : g[j]; }
+};
+
+// Cluster sizes from the labels (every CTA counts them itself: n reads); the
+// labels are kept in shared memory on the way when they fit.
+__device__ LabelView knn_label_counts(int n, const int *label, int *s_cnt /* [CMAX] */,
+                                      unsigned char *s_lab /* [KQ_LAB_CAP] */)
 {
+    const bool keep = n <= KQ_LAB_CAP;
     if (threadIdx.x < CMAX) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&s_cnt[label[i]], 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = label[i];
+        atomicAdd(&s_cnt[l], 1);
+        if (keep) s_lab[i] = (unsigned char)l;
+    }
     __syncthreads();
+    return LabelView{label, s_lab, keep};
 }
 
 // Queries of one CTA, grouped by label.  The n points are ordered by (label,
@@ -1006,7 +1028,7 @@ __device__ void knn_label_counts(int n, const int *label, int *s_cnt /* [CMAX] *
 // come from one or two clusters and it scans only candidates with those labels.
 // q_slot[32] receives the query indices (-1 past n); returns the label set as a
 // bit mask.  s_cnt: the label counts.
-__device__ unsigned long long knn_block_queries(int n, const int *label, int *q_slot, const int *s_cnt,
+__device__ unsigned long long knn_block_queries(int n, LabelView lab, int *q_slot, const int *s_cnt,
                                                 int *s_wsum /* [KQ_WARPS] */)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1025,7 +1047,7 @@ __device__ unsigned long long knn_block_queries(int n, const int *label, int *q_
             int base = 0;
             for (int i0 = 0; i0 < n && base < r1; i0 += blockDim.x) {
                 const int i = i0 + tid;
-                const bool f = (i < n) && label[i] == c;
+                const bool f = (i < n) && lab(i) == c;
                 const unsigned bal = __ballot_sync(0xffffffffu, f);
                 if (lane == 0) s_wsum[warp] = __popc(bal);
                 __syncthreads();
@@ -1047,26 +1069,66 @@ __device__ unsigned long long knn_block_queries(int n, const int *label, int *q_
     return mask;
 }
 
+// Merge the KQ_WARPS sorted lists of each lane's query (warp 0) and write ranks 1..KNN_K.
+__device__ __forceinline__ void knn_merge_write(const unsigned long long *merge, bool act, int i, int *nbr)
+{
+    const int lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) != 0) return;
+    int pos[KQ_WARPS];
+#pragma unroll
+    for (int w2 = 0; w2 < KQ_WARPS; ++w2) pos[w2] = 0;
+    for (int rnk = 0; rnk < KNN_K; ++rnk) {
+        unsigned long long best = ~0ull;
+        int bw = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
+            const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KQ_MSTRIDE + pos[w2]] : ~0ull;
+            if (v < best) {
+                best = v;
+                bw = w2;
+            }
+        }
+#pragma unroll
+        for (int w2 = 0; w2 < KQ_WARPS; ++w2)
+            if (w2 == bw) ++pos[w2];
+        if (act) nbr[(long)i * KNN_K + rnk] = (best == ~0ull) ? -1 : (int)(best & 0xffffffffu);
+    }
+}
+
+// Asynchronous global -> shared copies for the candidate tiles: 16 bytes with a
+// zero fill past src_bytes (4, 8, 12 or 16), or one float.
+__device__ __forceinline__ void cp_async16_fill(float *dst_smem, const float *src_gmem, int src_bytes)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src_gmem), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *dst_smem, const float *src_gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // QR: query components held in registers (d <= QR, QR a multiple of 4).  The
 // candidates whose label is one of the CTA's stream through shared memory in
-// tiles (compacted, ascending index, coalesced loads by the whole CTA); every
-// lane of a warp then reads the same row (a broadcast), two candidates at a
-// time for independent accumulation chains.
-constexpr int KQ_TILE = 128;
-static_assert(KQ_TILE == KQ_WARPS * 32, "one tile row per thread in the compaction");
-constexpr int KQ_MSTRIDE = KNN_K + 1;  // merge-list stride per lane (u64): spreads the banks
+// tiles (compacted, ascending index); every lane of a warp then reads the same
+// row (a broadcast), two candidates at a time for independent accumulation
+// chains.  Tiles are double-buffered: the rows of tile t + 1 are copied
+// asynchronously (cp.async) while tile t is scanned.
 
 template <int QR>
-__device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+__device__ void knn_lanes(const float *x, int xstride, int n, int d, LabelView lab, const int *csize, int *nbr,
                           unsigned long long *merge /* [KQ_WARPS][32][KQ_MSTRIDE] */,
-                          float *tile /* [KQ_TILE][QR] */, int *tidx /* [KQ_TILE] */, int *tlab /* [KQ_TILE] */,
-                          int *q_slot /* [32] */, int *s_wsum /* [KQ_WARPS] */)
+                          float *tile /* [2][KQ_TILE][QR], the same memory as merge */,
+                          int *tidx /* [2][KQ_TILE] */, int *tlab /* [2][KQ_TILE] */, int *q_slot /* [32] */,
+                          int *s_wsum /* [KQ_WARPS] */)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long lmask = knn_block_queries(n, label, q_slot, csize, s_wsum);
+    const unsigned long long lmask = knn_block_queries(n, lab, q_slot, csize, s_wsum);
     const int i = q_slot[lane];
     const bool act = i >= 0;
-    const int li = act ? label[i] : -1;
+    const int li = act ? lab(i) : -1;
     const bool need = act && csize[li] >= 3;
     const bool any_need = __syncthreads_or(need);
     float q[QR];
@@ -1080,111 +1142,108 @@ __device__ void knn_lanes(const float *x, int xstride, int n, int d, const int *
         Il[u] = -1;
     }
     if (any_need) {
-        for (int j0 = 0; j0 < n; j0 += KQ_TILE) {
-            // compact the candidates of this tile whose label belongs to the CTA
+        const bool vec = ((reinterpret_cast<size_t>(x) & 15u) == 0) && (xstride & 3) == 0;
+        // Compact the candidates [j0, j0 + KQ_TILE) whose label belongs to the CTA into
+        // buffer b and start the copies of their rows (zeros past d, and in the row past
+        // the last, which keeps the pair loop inside the tile).  Returns the row count.
+        auto stage = [&](int j0, int b) -> int {
             const int jj = j0 + threadIdx.x;  // KQ_TILE == blockDim.x
-            const int lj = (jj < n) ? label[jj] : -1;
+            const int lj = (jj < n) ? lab(jj) : -1;
             const bool f = lj >= 0 && ((lmask >> lj) & 1ull);
             const unsigned bal = __ballot_sync(0xffffffffu, f);
-            __syncthreads();  // the previous tile is no longer read
             if (lane == 0) s_wsum[warp] = __popc(bal);
-            __syncthreads();
+            __syncthreads();  // also: buffer b (the tile before the previous one) is no longer read
             int pos = __popc(bal & ((1u << lane) - 1u)), rows = 0;
             for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
                 pos += (w2 < warp) ? s_wsum[w2] : 0;
                 rows += s_wsum[w2];
             }
+            int *ti = tidx + b * KQ_TILE;
             if (f) {
-                tidx[pos] = jj;
-                tlab[pos] = lj;
+                ti[pos] = jj;
+                tlab[b * KQ_TILE + pos] = lj;
             }
-            if (rows == 0) continue;
             __syncthreads();
-            // rows padded with zeros up to QR (the query is zero there too); one row past
-            // the last keeps the pair loop inside the tile
+            float *tb = tile + b * KQ_TILE * QR;
             const int rows2 = min(rows + 1, KQ_TILE);
-            for (int e = threadIdx.x; e < rows2 * (QR / 4); e += blockDim.x) {
-                const int rr = e / (QR / 4), t4 = (e - rr * (QR / 4)) * 4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (rr < rows) {
-                    const float *row = x + (long)tidx[rr] * xstride;
-                    if (t4 + 0 < d) v.x = row[t4 + 0];
-                    if (t4 + 1 < d) v.y = row[t4 + 1];
-                    if (t4 + 2 < d) v.z = row[t4 + 2];
-                    if (t4 + 3 < d) v.w = row[t4 + 3];
+            if (vec) {
+                for (int e = threadIdx.x; e < rows2 * (QR / 4); e += blockDim.x) {
+                    const int rr = e / (QR / 4), t4 = (e - rr * (QR / 4)) * 4;
+                    float *dst = tb + rr * QR + t4;
+                    const int bytes = (rr < rows) ? 4 * max(0, min(d - t4, 4)) : 0;
+                    if (bytes > 0) cp_async16_fill(dst, x + (long)ti[rr] * xstride + t4, bytes);
+                    else *reinterpret_cast<float4 *>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                *reinterpret_cast<float4 *>(tile + rr * QR + t4) = v;
+            } else {
+                for (int e = threadIdx.x; e < rows2 * QR; e += blockDim.x) {
+                    const int rr = e / QR, t = e - rr * QR;
+                    float *dst = tb + rr * QR + t;
+                    if (rr < rows && t < d) cp_async4(dst, x + (long)ti[rr] * xstride + t);
+                    else *dst = 0.f;
+                }
             }
-            __syncthreads();
+            cp_async_commit();
+            return rows;
+        };
+        int rows = stage(0, 0);
+        for (int t = 0, j0 = 0; j0 < n; ++t, j0 += KQ_TILE) {
+            const int b = t & 1;
+            int rows_next = 0;
+            if (j0 + KQ_TILE < n) rows_next = stage(j0 + KQ_TILE, b ^ 1);
+            else cp_async_commit();  // an empty group keeps the wait below uniform
+            cp_async_wait_prev();    // this thread's copies of tile t have landed
+            __syncthreads();         // ... and every thread's
+            const float *tb = tile + b * KQ_TILE * QR;
+            const int *ti = tidx + b * KQ_TILE, *tl = tlab + b * KQ_TILE;
             for (int rr = warp * 2; rr < rows; rr += 2 * KQ_WARPS) {
-                const float *ra = tile + rr * QR;
-                const float *rb = tile + (rr + 1) * QR;  // inside the tile (zeros past the rows)
+                const float *ra = tb + rr * QR;
+                const float *rb = tb + (rr + 1) * QR;  // inside the tile (zeros past the rows)
                 float sa = 0.f, sb = 0.f;
 #pragma unroll
-                for (int t = 0; t < QR; t += 4) {
-                    const float4 va = *reinterpret_cast<const float4 *>(ra + t);
-                    const float4 vb = *reinterpret_cast<const float4 *>(rb + t);
-                    float da = __fsub_rn(q[t], va.x), db = __fsub_rn(q[t], vb.x);
+                for (int t4 = 0; t4 < QR; t4 += 4) {
+                    const float4 va = *reinterpret_cast<const float4 *>(ra + t4);
+                    const float4 vb = *reinterpret_cast<const float4 *>(rb + t4);
+                    float da = __fsub_rn(q[t4], va.x), db = __fsub_rn(q[t4], vb.x);
                     sa = __fmaf_rn(da, da, sa);
                     sb = __fmaf_rn(db, db, sb);
-                    da = __fsub_rn(q[t + 1], va.y);
-                    db = __fsub_rn(q[t + 1], vb.y);
+                    da = __fsub_rn(q[t4 + 1], va.y);
+                    db = __fsub_rn(q[t4 + 1], vb.y);
                     sa = __fmaf_rn(da, da, sa);
                     sb = __fmaf_rn(db, db, sb);
-                    da = __fsub_rn(q[t + 2], va.z);
-                    db = __fsub_rn(q[t + 2], vb.z);
+                    da = __fsub_rn(q[t4 + 2], va.z);
+                    db = __fsub_rn(q[t4 + 2], vb.z);
                     sa = __fmaf_rn(da, da, sa);
                     sb = __fmaf_rn(db, db, sb);
-                    da = __fsub_rn(q[t + 3], va.w);
-                    db = __fsub_rn(q[t + 3], vb.w);
+                    da = __fsub_rn(q[t4 + 3], va.w);
+                    db = __fsub_rn(q[t4 + 3], vb.w);
                     sa = __fmaf_rn(da, da, sa);
                     sb = __fmaf_rn(db, db, sb);
                 }
-                const int ja = tidx[rr];
-                if (need && tlab[rr] == li && ja != i) knn_push(Dl, Il, __float_as_uint(sa), ja);
+                const int ja = ti[rr];
+                if (need && tl[rr] == li && ja != i) knn_push(Dl, Il, __float_as_uint(sa), ja);
                 if (rr + 1 < rows) {
-                    const int jb = tidx[rr + 1];
-                    if (need && tlab[rr + 1] == li && jb != i) knn_push(Dl, Il, __float_as_uint(sb), jb);
+                    const int jb = ti[rr + 1];
+                    if (need && tl[rr + 1] == li && jb != i) knn_push(Dl, Il, __float_as_uint(sb), jb);
                 }
             }
+            rows = rows_next;
         }
+        __syncthreads();  // the merge lists below reuse the tile memory
     }
 #pragma unroll
     for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KQ_MSTRIDE + u] = knn_key(Dl[u], Il[u]);
     __syncthreads();
-    if (warp == 0) {
-        // merge the KQ_WARPS sorted lists of this lane's query
-        int pos[KQ_WARPS];
-#pragma unroll
-        for (int w2 = 0; w2 < KQ_WARPS; ++w2) pos[w2] = 0;
-        for (int rnk = 0; rnk < KNN_K; ++rnk) {
-            unsigned long long best = ~0ull;
-            int bw = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
-                const unsigned long long v =
-                    (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KQ_MSTRIDE + pos[w2]] : ~0ull;
-                if (v < best) {
-                    best = v;
-                    bw = w2;
-                }
-            }
-#pragma unroll
-            for (int w2 = 0; w2 < KQ_WARPS; ++w2)
-                if (w2 == bw) ++pos[w2];
-            if (act) nbr[(long)i * KNN_K + rnk] = (best == ~0ull) ? -1 : (int)(best & 0xffffffffu);
-        }
-    }
+    knn_merge_write(merge, act, i, nbr);
 }
 
 // Queries wider than the register budget: the query row is read from global memory.
-__device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const int *label, const int *csize, int *nbr,
+__device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, LabelView lab, const int *csize, int *nbr,
                                unsigned long long *merge)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * 32 + lane;
     const bool act = i < n;
-    const int li = act ? label[i] : -1;
+    const int li = act ? lab(i) : -1;
     const bool need = act && csize[li] >= 3;
     const float *qi = x + (long)(act ? i : 0) * xstride;
     uint32_t Dl[KNN_K];
@@ -1196,7 +1255,7 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
     }
     if (__any_sync(0xffffffffu, need)) {
         for (int j = warp; j < n; j += KQ_WARPS) {
-            const int lj = label[j];
+            const int lj = lab(j);
             const float s = sqdist_rn(qi, x + (long)j * xstride, d);
             if (need && lj == li && j != i) knn_push(Dl, Il, __float_as_uint(s), j);
         }
@@ -1204,47 +1263,39 @@ __device__ void knn_lanes_wide(const float *x, int xstride, int n, int d, const 
 #pragma unroll
     for (int u = 0; u < KNN_K; ++u) merge[(warp * 32 + lane) * KQ_MSTRIDE + u] = knn_key(Dl[u], Il[u]);
     __syncthreads();
-    if (warp == 0) {
-        int pos[KQ_WARPS];
-#pragma unroll
-        for (int w2 = 0; w2 < KQ_WARPS; ++w2) pos[w2] = 0;
-        for (int rnk = 0; rnk < KNN_K; ++rnk) {
-            unsigned long long best = ~0ull;
-            int bw = 0;
-#pragma unroll
-            for (int w2 = 0; w2 < KQ_WARPS; ++w2) {
-                const unsigned long long v = (pos[w2] < KNN_K) ? merge[(w2 * 32 + lane) * KQ_MSTRIDE + pos[w2]] : ~0ull;
-                if (v < best) {
-                    best = v;
-                    bw = w2;
-                }
-            }
-#pragma unroll
-            for (int w2 = 0; w2 < KQ_WARPS; ++w2)
-                if (w2 == bw) ++pos[w2];
-            if (act) nbr[(long)i * KNN_K + rnk] = (best == ~0ull) ? -1 : (int)(best & 0xffffffffu);
-        }
-    }
+    knn_merge_write(merge, act, i, nbr);
 }
 
-// shared memory: merge lists [KQ_WARPS][32][KQ_MSTRIDE] u64 | tile [KQ_TILE][64] f32 | tile indices and
-// labels [KQ_TILE] | query slots [32] | label counts [CMAX] | warp sums [KQ_WARPS].  The cluster sizes
-// come from the labels themselves, so the k-NN may run while the statistics are being updated.
+// Register width of the query for dimension d (0: the wide form).
+__host__ __device__ constexpr int knn_qr(int d) { return d <= 8 ? 8 : d <= 16 ? 16 : d <= 32 ? 32 : d <= 64 ? 64 : 0; }
+// Bytes of the region shared by the merge lists and the two candidate tiles.
+__host__ __device__ constexpr size_t knn_region_bytes(int d)
+{
+    return (sizeof(unsigned long long) * KQ_WARPS * 32 * KQ_MSTRIDE > sizeof(float) * 2 * KQ_TILE * knn_qr(d))
+               ? sizeof(unsigned long long) * KQ_WARPS * 32 * KQ_MSTRIDE
+               : sizeof(float) * 2 * KQ_TILE * knn_qr(d);
+}
+
+// shared memory: merge lists [KQ_WARPS][32][KQ_MSTRIDE] u64, in the same memory as the candidate tiles
+// [2][KQ_TILE][QR] f32 | tile indices and labels [2][KQ_TILE] each | query slots [32] | label counts
+// [CMAX] | warp sums [KQ_WARPS] | labels as bytes [KQ_LAB_CAP].  The cluster sizes come from the labels
+// themselves, so the k-NN may run while the statistics are being updated.
 __device__ void knn_rows(const float *x, int xstride, int n, int d, const int *label, int *nbr, float *smem)
 {
     unsigned long long *merge = reinterpret_cast<unsigned long long *>(smem);
-    float *tile = reinterpret_cast<float *>(merge + KQ_WARPS * 32 * KQ_MSTRIDE);
-    int *tidx = reinterpret_cast<int *>(tile + KQ_TILE * 64);
-    int *tlab = tidx + KQ_TILE;
-    int *q_slot = tlab + KQ_TILE;
+    float *tile = smem;
+    int *tidx = reinterpret_cast<int *>(reinterpret_cast<char *>(smem) + knn_region_bytes(d));
+    int *tlab = tidx + 2 * KQ_TILE;
+    int *q_slot = tlab + 2 * KQ_TILE;
     int *s_cnt = q_slot + 32;
     int *s_wsum = s_cnt + CMAX;
-    knn_label_counts(n, label, s_cnt);
-    if (d <= 8) knn_lanes<8>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
-    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
-    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
-    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, label, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
-    else knn_lanes_wide(x, xstride, n, d, label, s_cnt, nbr, merge);
+    unsigned char *s_lab = reinterpret_cast<unsigned char *>(s_wsum + KQ_WARPS);
+    const LabelView lab = knn_label_counts(n, label, s_cnt, s_lab);
+    if (d <= 8) knn_lanes<8>(x, xstride, n, d, lab, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 16) knn_lanes<16>(x, xstride, n, d, lab, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 32) knn_lanes<32>(x, xstride, n, d, lab, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else if (d <= 64) knn_lanes<64>(x, xstride, n, d, lab, s_cnt, nbr, merge, tile, tidx, tlab, q_slot, s_wsum);
+    else knn_lanes_wide(x, xstride, n, d, lab, s_cnt, nbr, merge);
 }
 
 __global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
@@ -1259,9 +1310,8 @@ __global__ void __launch_bounds__(KQ_WARPS * 32) k_knn(DevCtx C, int r0)
 
 size_t knn_smem_bytes(int d)
 {
-    (void)d;
-    return sizeof(unsigned long long) * (size_t)KQ_WARPS * 32 * KQ_MSTRIDE + sizeof(float) * KQ_TILE * 64 +
-           sizeof(int) * (2 * KQ_TILE + 32 + CMAX + KQ_WARPS);
+    // the region for the widest register form also covers every narrower run and the wide form
+    return knn_region_bytes(d < 64 ? d : 64) + sizeof(int) * (4 * KQ_TILE + 32 + CMAX + KQ_WARPS) + KQ_LAB_CAP;
 }
 
 // Union-find in shared memory: roots are the smallest member index.

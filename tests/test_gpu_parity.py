@@ -64,7 +64,10 @@ def test_sort_order_bit_exact(n):
 
 # ---------------------------------------------------------------- clustering
 @pytest.mark.parametrize("seed,m,d,k", [(1, 60, 3, 3), (2, 300, 8, 4), (3, 1000, 32, 4), (4, 40, 2, 1),
-                                        (5, 130, 16, 2), (6, 3, 2, 1)])
+                                        (5, 130, 16, 2), (6, 3, 2, 1),
+                                        # labels past the shared-memory copy; rows not 16-byte aligned;
+                                        # queries wider than the register forms
+                                        (7, 4500, 8, 3), (8, 200, 5, 3), (9, 4200, 33, 2), (10, 300, 70, 2)])
 def test_knn_components_bit_exact(seed, m, d, k):
     rng = np.random.default_rng(seed)
     centers = rng.uniform(-1, 1, (k, d))
