@@ -49,7 +49,7 @@ const KindLaunch &kind_launch(int kind)
 
 namespace {
 
-constexpr int GRAPH_ITERS = 8;
+constexpr int GRAPH_ITERS = 16;
 constexpr size_t SMEM_LIMIT = 200 * 1024;
 constexpr size_t COOP_SMEM_LIMIT = 227 * 1024;  // one CTA per SM: the whole opt-in shared memory
 constexpr int NOISE_BLOCKS_PER_RUN = 64;
@@ -76,7 +76,7 @@ struct Group {
     std::vector<RunClass> classes;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
-    cudaEvent_t ev[8][2] = {};
+    cudaEvent_t ev[GRAPH_ITERS][2] = {};
     cudaEvent_t done_ev = nullptr;
     // the statistics update runs on a second stream, beside the HSS phases
     cudaStream_t ev_stream = nullptr;
