@@ -836,9 +836,14 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                         }
                     }
                 }
-                CU(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
-                CU(cudaStreamCreateWithFlags(&g.ev_stream, cudaStreamNonBlocking));
-                CU(cudaStreamCreateWithFlags(&g.nz_stream, cudaStreamNonBlocking));
+                // the iteration's chain (k-NN, selection, HSS, pick, tail) runs at the highest
+                // priority: CTAs of the side streams (noise drawn ahead, statistics) take the SMs
+                // only where the chain leaves room, instead of delaying it
+                int prio_low = 0, prio_high = 0;
+                CU(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+                CU(cudaStreamCreateWithPriority(&g.stream, cudaStreamNonBlocking, prio_high));
+                CU(cudaStreamCreateWithPriority(&g.ev_stream, cudaStreamNonBlocking, prio_low));
+                CU(cudaStreamCreateWithPriority(&g.nz_stream, cudaStreamNonBlocking, prio_low));
                 CU(cudaEventCreateWithFlags(&g.nz_fork_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.nz_join_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.fork_ev, cudaEventDisableTiming));
@@ -938,7 +943,7 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
             return s;
         }
         CU(cudaStreamEndCapture(g.stream, &gr));
-        CU(cudaGraphInstantiate(&g.graph, gr, 0));
+        CU(cudaGraphInstantiateWithFlags(&g.graph, gr, cudaGraphInstantiateFlagUseNodePriority));
         cudaGraphDestroy(gr);
     }
     long done_iters = 0;

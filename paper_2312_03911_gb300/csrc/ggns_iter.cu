@@ -130,17 +130,134 @@ struct EvScratch {
     double wtot[EV_CB][EV_THREADS / 32];
     double coef[EV_CB][CMAX];
     double S1[CMAX], S2[CMAX], U[CMAX], V[CMAX];
+    // per-cluster logs: lg = {log(n+1), log(n+2), log(r+1), log(r+2)} with r = n - m (-inf when r <= 0),
+    // lq = {log S1, log S2, log V, log(U + S2)}
+    double lg[4][CMAX], lq[4][CMAX];
     int m[CMAX];
     int alive_list[CMAX];
     int n_alive;
-    double lref;
+    double lref, lxref;
     double new_logZp[CMAX], new_logZp2[CMAX], new_logZXp[CMAX], new_logZpXp[CMAX], new_logXp[CMAX],
-        new_logXp2[CMAX], dZ[CMAX], dZ2[CMAX], logw[CMAX];
+        new_logXp2[CMAX], dZ[CMAX], dZ2[CMAX], dZp2[CMAX], logw[CMAX];
 };
 
+// On this GPU one FP64 warp instruction occupies the SM sub-partition's FP64
+// pipe for many cycles whatever the number of active lanes, so the update below
+// keeps FP64 transcendentals few and spread over lanes: per-cluster logs are
+// tabled once (one lane each), the five log-sums of every cluster run on
+// separate lanes, and the kill passes carry only as many target clusters as
+// there are (NB = 1, 2, 4 or 8).
+
+// S1, S2, U, V of the nb target clusters tgt[0..nb) (NB >= nb) over the kills
+// (see the comment above EvScratch); writes E->S1/S2/U/V of the targets.
+template <int NB>
+__device__ void evidence_kill_pass(int k, const double *kL, const int *kP, EvScratch *E, const int *tgt_list, int nb,
+                                   double lref, bool have_l)
+{
+    const int tid = threadIdx.x;
+    const int ch = (k + EV_THREADS - 1) / EV_THREADS;
+    const int j0 = min(k, tid * ch), j1 = min(k, j0 + ch);
+    double R[NB], Vl[NB], Ul[NB], S1l[NB], S2l[NB];
+    int tgt[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        R[b] = Vl[b] = Ul[b] = S1l[b] = S2l[b] = 0.0;
+        tgt[b] = (b < nb) ? tgt_list[b] : -1;
+    }
+    if (tid < EV_THREADS) {
+        for (int j = j0; j < j1; ++j) {
+            const int q = kP[j];
+            const double l = (have_l && kL[j] == kL[j]) ? exp(kL[j] - lref) : 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                if (tgt[b] == q) {
+                    Vl[b] += l * R[b];
+                    Ul[b] += l * S1l[b];
+                    S1l[b] += l;
+                    S2l[b] += l * l;
+                }
+                R[b] += E->coef[b][q] * l;
+            }
+        }
+    }
+    // exclusive scans over threads of R and S1: warp shuffle scans, then the
+    // warp totals in order (a fixed order: deterministic)
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
+        double v[NB], x[NB];
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb) x[bb] = v[bb] = (pass == 0) ? R[bb] : S1l[bb];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) {
+                const double y = __shfl_up_sync(0xffffffffu, x[bb], o);
+                if (lane >= o) x[bb] += y;
+            }
+        }
+        if (lane == 31) {
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) E->wtot[bb][warp] = x[bb];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb) {
+            double off = 0.0;
+            for (int w2 = 0; w2 < warp; ++w2) off += E->wtot[bb][w2];
+            const double excl = off + x[bb] - v[bb];
+            if (pass == 0) Vl[bb] += S1l[bb] * excl;
+            else Ul[bb] += S1l[bb] * excl;
+        }
+        __syncthreads();
+    }
+    // reductions over threads: warp trees, then the warp partials in order
+    for (int qty = 0; qty < 4; ++qty) {
+        double x[NB];
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb)
+            x[bb] = qty == 0 ? S1l[bb] : (qty == 1 ? S2l[bb] : (qty == 2 ? Ul[bb] : Vl[bb]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) x[bb] += __shfl_xor_sync(0xffffffffu, x[bb], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb) E->wtot[bb][warp] = x[bb];
+        }
+        __syncthreads();
+        if (tid < nb) {
+            double sacc = 0.0;
+            for (int w2 = 0; w2 < EV_THREADS / 32; ++w2) sacc += E->wtot[tid][w2];
+            const int c = tgt_list[tid];
+            if (qty == 0) E->S1[c] = sacc;
+            else if (qty == 1) E->S2[c] = sacc;
+            else if (qty == 2) E->U[c] = sacc;
+            else E->V[c] = sacc;
+        }
+        __syncthreads();
+    }
+}
+
+// log(sum_i exp(t_i)) of the n terms term(0..n-1), by the largest term and one
+// log; -inf when every term is -inf.
+template <typename F>
+__device__ __forceinline__ double log_sum(int n, F term)
+{
+    double m = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+        const double t = term(i);
+        m = (t > m) ? t : m;
+    }
+    if (m == -INFINITY) return -INFINITY;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += exp(term(i) - m);
+    return m + log(s);
+}
+
 // kL[j] (FP64 log-likelihoods, ascending) and kP[j] (labels), j < k.  Updates
-// st in place (the whole CTA calls it).  logw_of_cluster receives the log prior
-// mass per kill of each cluster.  Returns nothing; st->n and st->alive updated.
+// st in place (the whole CTA calls it).  E->logw receives the log prior mass per
+// kill of each cluster.  st->n and st->alive are updated.
 __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, const double *kL, const int *kP,
                                EvScratch *E)
 {
@@ -151,9 +268,15 @@ __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, co
     }
     if (tid == 0) {
         int na = 0;
+        double lx = -INFINITY;
         for (int c = 0; c < CMAX; ++c)
-            if (st->alive[c]) E->alive_list[na++] = c;
+            if (st->alive[c]) {
+                E->alive_list[na++] = c;
+                lx = fmax(lx, st->logXp[c]);
+            }
         E->n_alive = na;
+        // X_ref: largest cluster volume (keeps the coefficients a_{c,q} <= ~1)
+        E->lxref = lx;
         // L_ref: largest finite log-likelihood of the batch
         double lr = -INFINITY;
         for (int j = k - 1; j >= 0; --j) {
@@ -167,180 +290,130 @@ __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, co
     __syncthreads();
     for (int j = tid; j < k; j += blockDim.x) atomicAdd(&E->m[kP[j]], 1);
     __syncthreads();
-    const double lref = E->lref;
+    const double lref = E->lref, lxref = E->lxref;
     const bool have_l = lref > -INFINITY && lref < INFINITY;
     const int nA = E->n_alive;
-    // X_ref: largest cluster volume (keeps the coefficients a_{c,q} <= ~1)
-    double lxref = -INFINITY;
-    for (int a = 0; a < nA; ++a) lxref = fmax(lxref, st->logXp[E->alive_list[a]]);
-
-    const int ch = (k + EV_THREADS - 1) / EV_THREADS;
-    const int j0 = min(k, tid * ch), j1 = min(k, j0 + ch);
-    for (int pb = 0; pb < nA; pb += EV_CB) {
-        const int nb = min(EV_CB, nA - pb);
-        // coefficient table for the target clusters of this pass
-        for (int i = tid; i < EV_CB * CMAX; i += blockDim.x) {
-            const int b = i / CMAX, q = i % CMAX;
-            double v = 0.0;
-            if (b < nb && st->alive[q]) {
-                const int c = E->alive_list[pb + b];
-                double lc;
-                if (q == c) lc = st->logXp2[c] - log((double)st->n[c] + 2.0) - st->logXp[c];
-                else lc = st->logXX[q * CMAX + c] - log((double)st->n[q] + 1.0) - st->logXp[c];
-                v = exp(lc - lxref);
-            }
-            E->coef[b][q] = v;
-        }
-        __syncthreads();
-        double R[EV_CB], Vl[EV_CB], Ul[EV_CB], S1l[EV_CB], S2l[EV_CB];
-        int tgt[EV_CB];
-#pragma unroll
-        for (int b = 0; b < EV_CB; ++b) {
-            R[b] = Vl[b] = Ul[b] = S1l[b] = S2l[b] = 0.0;
-            tgt[b] = (b < nb) ? E->alive_list[pb + b] : -1;
-        }
-        if (tid < EV_THREADS) {
-            for (int j = j0; j < j1; ++j) {
-                const int q = kP[j];
-                const double l = (have_l && kL[j] == kL[j]) ? exp(kL[j] - lref) : 0.0;
-#pragma unroll
-                for (int b = 0; b < EV_CB; ++b) {
-                    if (tgt[b] == q) {
-                        Vl[b] += l * R[b];
-                        Ul[b] += l * S1l[b];
-                        S1l[b] += l;
-                        S2l[b] += l * l;
-                    }
-                    R[b] += E->coef[b][q] * l;
-                }
-            }
-        }
-        // exclusive scans over threads of R and S1: warp shuffle scans, then the
-        // eight warp totals in order (a fixed order: deterministic)
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int pass = 0; pass < 2; ++pass) {
-            double v[EV_CB], x[EV_CB];
-#pragma unroll
-            for (int bb = 0; bb < EV_CB; ++bb) x[bb] = v[bb] = (pass == 0) ? R[bb] : S1l[bb];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-                for (int bb = 0; bb < EV_CB; ++bb) {
-                    const double y = __shfl_up_sync(0xffffffffu, x[bb], o);
-                    if (lane >= o) x[bb] += y;
-                }
-            }
-            if (lane == 31) {
-#pragma unroll
-                for (int bb = 0; bb < EV_CB; ++bb) E->wtot[bb][warp] = x[bb];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int bb = 0; bb < EV_CB; ++bb) {
-                double off = 0.0;
-                for (int w2 = 0; w2 < warp; ++w2) off += E->wtot[bb][w2];
-                const double excl = off + x[bb] - v[bb];
-                if (pass == 0) Vl[bb] += S1l[bb] * excl;
-                else Ul[bb] += S1l[bb] * excl;
-            }
-            __syncthreads();
-        }
-        // reductions over threads: warp trees, then the warp partials in order
-        for (int qty = 0; qty < 4; ++qty) {
-            double x[EV_CB];
-#pragma unroll
-            for (int bb = 0; bb < EV_CB; ++bb)
-                x[bb] = qty == 0 ? S1l[bb] : (qty == 1 ? S2l[bb] : (qty == 2 ? Ul[bb] : Vl[bb]));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int bb = 0; bb < EV_CB; ++bb) x[bb] += __shfl_xor_sync(0xffffffffu, x[bb], o);
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int bb = 0; bb < EV_CB; ++bb) E->wtot[bb][warp] = x[bb];
-            }
-            __syncthreads();
-            if (tid < nb) {
-                double sacc = 0.0;
-                for (int w2 = 0; w2 < EV_THREADS / 32; ++w2) sacc += E->wtot[tid][w2];
-                const int c = E->alive_list[pb + tid];
-                if (qty == 0) E->S1[c] = sacc;
-                else if (qty == 1) E->S2[c] = sacc;
-                else if (qty == 2) E->U[c] = sacc;
-                else E->V[c] = sacc;
-            }
-            __syncthreads();
-        }
-    }
-    // closed-form update of every live cluster (all right-hand sides old values)
-    const double LN2 = 0.69314718055994530942;
-    if (tid < CMAX && st->alive[tid]) {
-        const int c = tid;
-        const double n = (double)st->n[c];
-        const int mc = E->m[c];
-        const double Xc = st->logXp[c], X2c = st->logXp2[c];
-        const double ln1 = log(n + 1.0), ln2 = log(n + 2.0);
-        const double lS1 = log(E->S1[c]), lS2 = log(E->S2[c]), lU = log(E->U[c]), lV = log(E->V[c]);
-        const double L = lref;
-        E->logw[c] = Xc - ln1;
-        // update0/1 summed: dZ_c = X_c S1_c e^L / (n_c + 1)
-        const double dZ = (mc > 0 && have_l) ? Xc - ln1 + lS1 + L : -INFINITY;
-        E->dZ[c] = dZ;
-        // update3 summed: 2 e^L ZX_c S1/(n+1) + 2 e^2L X_c X_ref V/(n+1) + 2 e^2L X2_c S2/((n+1)(n+2))
-        double dZ2 = -INFINITY;
-        if (mc > 0 && have_l) {
-            dZ2 = log_add(dZ2, LN2 + L + st->logZXp[c] + lS1 - ln1);
-            dZ2 = log_add(dZ2, LN2 + 2.0 * L + Xc + lxref + lV - ln1);
-            dZ2 = log_add(dZ2, LN2 + 2.0 * L + X2c + lS2 - ln1 - ln2);
-        }
-        E->dZ2[c] = dZ2;
-        // update4 summed: 2 e^L Z_cX_c S1/(n+1) + 2 e^2L X2_c (U + S2)/((n+1)(n+2))
-        double dZp2 = -INFINITY;
-        if (mc > 0 && have_l) {
-            dZp2 = log_add(dZp2, LN2 + L + st->logZpXp[c] + lS1 - ln1);
-            dZp2 = log_add(dZp2, LN2 + 2.0 * L + X2c + log_add(lU, lS2) - ln1 - ln2);
-        }
-        const double nr = n - (double)mc;  // live count after the batch
-        const double lrho = (nr > 0.0) ? log(nr + 1.0) - ln1 : -INFINITY;
-        // update5/6: ZX_c -> rho (ZX_c + e^L [X2_c S1_c/(n_c+2) + sum_{q != c} XX_qc S1_q/(n_q+1)])
-        double inner = st->logZXp[c];
-        if (have_l) {
-            if (mc > 0) inner = log_add(inner, L + X2c + lS1 - ln2);
-            for (int q = 0; q < CMAX; ++q) {
-                if (q == c || !st->alive[q] || E->m[q] == 0) continue;
-                inner = log_add(inner, L + st->logXX[q * CMAX + c] + log(E->S1[q]) - log((double)st->n[q] + 1.0));
-            }
-        }
-        E->new_logZXp[c] = (nr > 0.0) ? inner + lrho : -INFINITY;
-        // update7: Z_cX_c -> rho (Z_cX_c + e^L X2_c S1_c/(n_c+2))
-        double inner2 = st->logZpXp[c];
-        if (have_l && mc > 0) inner2 = log_add(inner2, L + X2c + lS1 - ln2);
-        E->new_logZpXp[c] = (nr > 0.0) ? inner2 + lrho : -INFINITY;
-        E->new_logZp[c] = log_add(st->logZp[c], dZ);
-        E->new_logZp2[c] = log_add(st->logZp2[c], dZp2);
-        E->new_logXp[c] = Xc + lrho;
-        E->new_logXp2[c] = (nr > 0.0) ? X2c + log(nr + 1.0) + log(nr + 2.0) - ln1 - ln2 : -INFINITY;
+    // per-cluster count logs, one lane each
+    for (int i = tid; i < 4 * nA; i += blockDim.x) {
+        const int which = i / nA, c = E->alive_list[i - which * nA];
+        const double n = (double)st->n[c], r = n - (double)E->m[c];
+        double v;
+        if (which == 0) v = log(n + 1.0);
+        else if (which == 1) v = log(n + 2.0);
+        else if (r <= 0.0) v = -INFINITY;
+        else v = log(r + (which == 2 ? 1.0 : 2.0));
+        E->lg[which][c] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        double z = *logZ, z2 = *logZ2;
-        for (int c = 0; c < CMAX; ++c) {
-            if (!st->alive[c]) continue;
-            z = log_add(z, E->dZ[c]);
-            z2 = log_add(z2, E->dZ2[c]);
+    for (int pb = 0; pb < nA; pb += EV_CB) {
+        const int nb = min(EV_CB, nA - pb);
+        // coefficient table a_{c,q} / X_ref for the target clusters c of this pass
+        for (int i = tid; i < EV_CB * CMAX; i += blockDim.x) (&E->coef[0][0])[i] = 0.0;
+        __syncthreads();
+        for (int i = tid; i < nb * nA; i += blockDim.x) {
+            const int b = i / nA, q = E->alive_list[i - b * nA], c = E->alive_list[pb + b];
+            const double lc = (q == c) ? st->logXp2[c] - E->lg[1][c] - st->logXp[c]
+                                       : st->logXX[q * CMAX + c] - E->lg[0][q] - st->logXp[c];
+            E->coef[b][q] = exp(lc - lxref);
         }
-        *logZ = z;
-        *logZ2 = z2;
+        __syncthreads();
+        const int *tl = E->alive_list + pb;
+        if (nb <= 1) evidence_kill_pass<1>(k, kL, kP, E, tl, nb, lref, have_l);
+        else if (nb <= 2) evidence_kill_pass<2>(k, kL, kP, E, tl, nb, lref, have_l);
+        else if (nb <= 4) evidence_kill_pass<4>(k, kL, kP, E, tl, nb, lref, have_l);
+        else evidence_kill_pass<8>(k, kL, kP, E, tl, nb, lref, have_l);
+    }
+    // logs of the batch sums, one lane each
+    for (int i = tid; i < 4 * nA; i += blockDim.x) {
+        const int which = i / nA, c = E->alive_list[i - which * nA];
+        double v;
+        if (which == 0) v = log(E->S1[c]);
+        else if (which == 1) v = log(E->S2[c]);
+        else if (which == 2) v = log(E->V[c]);
+        else v = log(E->U[c] + E->S2[c]);
+        E->lq[which][c] = v;
+    }
+    __syncthreads();
+    // closed-form update of every live cluster (all right-hand sides old values):
+    // five independent log-sums per cluster, one lane each
+    const double LN2 = 0.69314718055994530942;
+    const double L = lref;
+    for (int i = tid; i < 5 * nA; i += blockDim.x) {
+        const int which = i / nA, c = E->alive_list[i - which * nA];
+        const int mc = E->m[c];
+        const bool batch = mc > 0 && have_l;
+        const double Xc = st->logXp[c], X2c = st->logXp2[c];
+        const double ln1 = E->lg[0][c], ln2 = E->lg[1][c];
+        const double lS1 = E->lq[0][c];
+        if (which == 0) {
+            // update3 summed: 2 e^L ZX_c S1/(n+1) + 2 e^2L X_c X_ref V/(n+1) + 2 e^2L X2_c S2/((n+1)(n+2))
+            double dZ2 = -INFINITY;
+            if (batch) {
+                dZ2 = log_add(dZ2, LN2 + L + st->logZXp[c] + lS1 - ln1);
+                dZ2 = log_add(dZ2, LN2 + 2.0 * L + Xc + lxref + E->lq[2][c] - ln1);
+                dZ2 = log_add(dZ2, LN2 + 2.0 * L + X2c + E->lq[1][c] - ln1 - ln2);
+            }
+            E->dZ2[c] = dZ2;
+        } else if (which == 1) {
+            // update4 summed: 2 e^L Z_cX_c S1/(n+1) + 2 e^2L X2_c (U + S2)/((n+1)(n+2))
+            double dZp2 = -INFINITY;
+            if (batch) {
+                dZp2 = log_add(dZp2, LN2 + L + st->logZpXp[c] + lS1 - ln1);
+                dZp2 = log_add(dZp2, LN2 + 2.0 * L + X2c + E->lq[3][c] - ln1 - ln2);
+            }
+            E->dZp2[c] = dZp2;
+        } else if (which == 2) {
+            // update5/6: ZX_c -> rho (ZX_c + e^L [X2_c S1_c/(n_c+2) + sum_{q != c} XX_qc S1_q/(n_q+1)])
+            double inner = st->logZXp[c];
+            if (have_l) {
+                // terms: ZX_c, the cluster's own kills, then the other clusters with kills (ascending q)
+                const int a = i - which * nA;  // c's place in the alive list
+                inner = log_sum(nA + 1, [&](int t) -> double {
+                    if (t == 0) return st->logZXp[c];
+                    if (t == 1) return mc > 0 ? L + X2c + lS1 - ln2 : -INFINITY;
+                    const int q = E->alive_list[(t - 2 < a) ? t - 2 : t - 1];
+                    return E->m[q] > 0 ? L + st->logXX[q * CMAX + c] + E->lq[0][q] - E->lg[0][q] : -INFINITY;
+                });
+            }
+            const double lrho = E->lg[2][c] - ln1;
+            E->new_logZXp[c] = (E->lg[2][c] > -INFINITY) ? inner + lrho : -INFINITY;
+        } else if (which == 3) {
+            // update7: Z_cX_c -> rho (Z_cX_c + e^L X2_c S1_c/(n_c+2))
+            double inner2 = st->logZpXp[c];
+            if (batch) inner2 = log_add(inner2, L + X2c + lS1 - ln2);
+            const double lrho = E->lg[2][c] - ln1;
+            E->new_logZpXp[c] = (E->lg[2][c] > -INFINITY) ? inner2 + lrho : -INFINITY;
+        } else {
+            // update0/1 summed: dZ_c = X_c S1_c e^L / (n_c + 1)
+            const double dZ = batch ? Xc - ln1 + lS1 + L : -INFINITY;
+            E->dZ[c] = dZ;
+            E->new_logZp[c] = log_add(st->logZp[c], dZ);
+            E->logw[c] = Xc - ln1;
+            const bool left = E->lg[2][c] > -INFINITY;  // points of c survive the batch
+            const double lrho = left ? E->lg[2][c] - ln1 : -INFINITY;
+            E->new_logXp[c] = Xc + lrho;
+            E->new_logXp2[c] = left ? X2c + E->lg[2][c] + E->lg[3][c] - ln1 - ln2 : -INFINITY;
+        }
+    }
+    __syncthreads();
+    // second level: Z_c^2 of every cluster, log Z and log Z^2 of the run (one lane each)
+    for (int i = tid; i < nA + 2; i += blockDim.x) {
+        if (i < nA) {
+            const int c = E->alive_list[i];
+            E->new_logZp2[c] = log_add(st->logZp2[c], E->dZp2[c]);
+        } else {
+            const double *d = (i == nA) ? E->dZ : E->dZ2;
+            double *out = (i == nA) ? logZ : logZ2;
+            const double z0 = *out;
+            *out = log_sum(nA + 1, [&](int t) -> double { return t == 0 ? z0 : d[E->alive_list[t - 1]]; });
+        }
     }
     // update9 for the cross moments (old counts), then commit
     for (int i = tid; i < CMAX * CMAX; i += blockDim.x) {
         const int c = i / CMAX, q = i % CMAX;
         if (c == q || !st->alive[c] || !st->alive[q]) continue;
-        const double nc = (double)st->n[c], nq = (double)st->n[q];
-        const double rc = nc - E->m[c], rq = nq - E->m[q];
-        if (rc <= 0.0 || rq <= 0.0) st->logXX[i] = -INFINITY;
-        else st->logXX[i] += log(rc + 1.0) - log(nc + 1.0) + log(rq + 1.0) - log(nq + 1.0);
+        if (E->lg[2][c] == -INFINITY || E->lg[2][q] == -INFINITY) st->logXX[i] = -INFINITY;
+        else st->logXX[i] += E->lg[2][c] - E->lg[0][c] + E->lg[2][q] - E->lg[0][q];
     }
     __syncthreads();
     if (tid < CMAX && st->alive[tid]) {
@@ -776,18 +849,30 @@ __global__ void __launch_bounds__(SEL_THREADS) k_evidence(DevCtx C, int r0)
     __syncthreads();
     if (tid < CMAX && st->alive[tid]) st->n[tid] += S->spawn_cnt[tid];
     __syncthreads();
-    if (tid == 0) {
-        // XL statistic on the dead-point sequence: log X (after the kills) + L*
-        double lx = -INFINITY;
+    if (tid < 32) {
+        // XL statistic on the dead-point sequence: log X (after the kills) + L*, as
+        // one log-sum over the live clusters (their exponentials one lane each)
+        double m = -INFINITY;
         int na = 0;
-        for (int c = 0; c < CMAX; ++c)
+        for (int c = tid; c < CMAX; c += 32)
             if (st->alive[c]) {
-                lx = log_add(lx, st->logXp[c]);
+                m = fmax(m, st->logXp[c]);
                 ++na;
             }
-        S->log_xl = lx + S->lstar;
-        S->n_clusters = na;
-        S->ev_pending = 0;
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            na += __shfl_xor_sync(0xffffffffu, na, o);
+        }
+        double e = 0.0;
+        if (m > -INFINITY)
+            for (int c = tid; c < CMAX; c += 32)
+                if (st->alive[c]) e += exp(st->logXp[c] - m);
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (tid == 0) {
+            S->log_xl = ((m > -INFINITY) ? m + log(e) : -INFINITY) + S->lstar;
+            S->n_clusters = na;
+            S->ev_pending = 0;
+        }
     }
     {
         const int4 *src = reinterpret_cast<const int4 *>(st);

@@ -107,7 +107,10 @@ def test_knn_components_lattice_ties():
 
 # ---------------------------------------------------------------- statistics
 @pytest.mark.parametrize("seed,counts,k", [(0, [500], 250), (1, [30, 50, 20], 50), (2, [7, 3, 9, 11], 24),
-                                           (3, [1000, 3], 501)])
+                                           (3, [1000, 3], 501),
+                                           # six target clusters in one pass; eleven in two passes (8 + 3)
+                                           (4, [40, 25, 33, 18, 51, 29], 90),
+                                           (5, [12, 17, 9, 22, 30, 15, 11, 26, 19, 14, 8], 120)])
 def test_evidence_statistics_match_sequential_update(seed, counts, k):
     rng = np.random.default_rng(seed)
     nc = len(counts)
