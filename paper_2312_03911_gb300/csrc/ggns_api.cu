@@ -84,7 +84,10 @@ struct Group {
     // the momentum noise of the single-pass HSS is drawn on a third stream
     cudaStream_t nz_stream = nullptr;
     cudaEvent_t nz_fork_ev = nullptr, nz_join_ev = nullptr;
-    int launches_per_iter = 0;
+    // the iteration's tail runs on the noise stream after the pick, beside the next k-NN
+    cudaEvent_t pick_ev = nullptr, tail_ev = nullptr;
+    int launches_per_iter = 0;    // kernels of the last launched iteration
+    int launches_per_replay = 0;  // kernels of one replay of the captured graph
 };
 
 struct DeadHost {
@@ -355,51 +358,67 @@ ns_status ensure_dead_capacity(ns_ctx *ctx, int iters, const std::vector<RunStat
 // The termination test of the previous iteration, once its statistics are in.
 ns_status launch_term_join(ns_ctx *ctx, Group &g, cudaStream_t s)
 {
+    CU(cudaStreamWaitEvent(s, g.tail_ev, 0));
     CU(cudaStreamWaitEvent(s, g.join_ev, 0));
     CU(launch_term(ctx->dc, g.r0, g.nr, s));
     return NS_OK;
 }
 
-// One iteration of Algorithm 3 for the runs of group g.  Unless `first`, the
-// previous iteration's statistics (on the second stream) are joined after this
-// iteration's k-NN, and its termination test runs then; a launch sequence ends
-// with launch_term_join.
-ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, bool first)
+// The momentum noise of the next iteration, drawn ahead on the noise stream.
+static ns_status launch_noise_ahead(ns_ctx *ctx, Group &g, int &n)
+{
+    for (auto &cl : g.classes)
+        if (cl.single) {
+            CU(launch_noise(ctx->dc, cl.runs_dev, (int)cl.runs.size(), NOISE_BLOCKS_PER_RUN, ctx->rec,
+                            ctx->rec_base_dev, g.nz_stream));
+            ++n;
+        }
+    CU(cudaEventRecord(g.nz_join_ev, g.nz_stream));
+    return NS_OK;
+}
+
+// One iteration of Algorithm 3 for the runs of group g, from the k-NN to the pick,
+// on stream s.  Unless `first`, the previous iteration's tail (on the noise
+// stream) and statistics (on the second stream) are joined after this
+// iteration's k-NN, and its termination test runs then.  The tail and, unless
+// `last`, the next iteration's noise follow the pick on the noise stream, beside
+// the next k-NN.  A launch sequence ends with launch_term_join.
+ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, bool first, bool last)
 {
     const DevCtx &C = ctx->dc;
     int n = 0;
     bool any_single = false;
     for (auto &cl : g.classes) any_single |= (cl.single != 0);
     const bool noise_ahead = any_single && ctx->rec.nT > 0;
-    if (noise_ahead) {
+    if (noise_ahead && first) {
         // fork: this iteration's momentum noise beside cluster finding and selection
         CU(cudaEventRecord(g.nz_fork_ev, s));
         CU(cudaStreamWaitEvent(g.nz_stream, g.nz_fork_ev, 0));
-        for (auto &cl : g.classes)
-            if (cl.single) {
-                CU(launch_noise(C, cl.runs_dev, (int)cl.runs.size(), NOISE_BLOCKS_PER_RUN, ctx->rec, ctx->rec_base_dev,
-                                g.nz_stream));
-                ++n;
-            }
-        CU(cudaEventRecord(g.nz_join_ev, g.nz_stream));
+        ns_status ns = launch_noise_ahead(ctx, g, n);
+        if (ns != NS_OK) return ns;
     }
     if (ctx->any_clustering) {
         CU(launch_knn(C, g.r0, g.nr, g.max_n, ctx->knn_smem, s));
         ++n;
     }
-    // the previous iteration's termination test once its statistics are in, then
-    // cluster finding and selection: one kernel per run
-    if (!first) CU(cudaStreamWaitEvent(s, g.join_ev, 0));
+    // the previous iteration's tail and termination test once its statistics are in,
+    // then cluster finding and selection: one kernel per run
+    if (!first) {
+        CU(cudaStreamWaitEvent(s, g.tail_ev, 0));
+        CU(cudaStreamWaitEvent(s, g.join_ev, 0));
+    }
     CU(launch_term_cluster_sort(C, g.r0, g.nr, ctx->lastkey, std::max(ctx->cl_smem, ctx->sort_smem), !first,
                                 ctx->any_clustering, s));
     ++n;
     // fork: the FP64 statistics of this iteration's kills beside the HSS phases
+    // (the timing events around the HSS are recorded on the side streams at the same
+    // points of the chain, so that no event node sits between two of its kernels)
     CU(cudaEventRecord(g.fork_ev, s));
     CU(cudaStreamWaitEvent(g.ev_stream, g.fork_ev, 0));
+    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][0], g.ev_stream, cudaEventRecordExternal));
     CU(launch_evidence(C, g.r0, g.nr, ctx->sel_smem, g.ev_stream));
     CU(cudaEventRecord(g.join_ev, g.ev_stream));
     ++n;
-    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][0], s, cudaEventRecordExternal));
     if (noise_ahead) CU(cudaStreamWaitEvent(s, g.nz_join_ev, 0));
     // single pass where every walker block of the class is resident, then the
     // three phases (for single-pass classes only if the records overflowed)
@@ -425,9 +444,17 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
                                         cl.single ? (phase | 4) : phase, cl.smem, cl.prec_in_smem, s));
             ++n;
         }
-    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][1], s, cudaEventRecordExternal));
-    CU(launch_tail(C, g.r0, g.nr, s));
+    // fork: the tail (step size, counters, iteration count), then the next iteration's noise
+    CU(cudaEventRecord(g.pick_ev, s));
+    CU(cudaStreamWaitEvent(g.nz_stream, g.pick_ev, 0));
+    if (ev_slot >= 0) CU(cudaEventRecordWithFlags(g.ev[ev_slot][1], g.nz_stream, cudaEventRecordExternal));
+    CU(launch_tail(C, g.r0, g.nr, g.nz_stream));
+    CU(cudaEventRecord(g.tail_ev, g.nz_stream));
     ++n;
+    if (noise_ahead && !last) {
+        ns_status ns = launch_noise_ahead(ctx, g, n);
+        if (ns != NS_OK) return ns;
+    }
     g.launches_per_iter = n;
     return NS_OK;
 }
@@ -846,6 +873,8 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 CU(cudaStreamCreateWithPriority(&g.nz_stream, cudaStreamNonBlocking, prio_low));
                 CU(cudaEventCreateWithFlags(&g.nz_fork_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.nz_join_ev, cudaEventDisableTiming));
+                CU(cudaEventCreateWithFlags(&g.pick_ev, cudaEventDisableTiming));
+                CU(cudaEventCreateWithFlags(&g.tail_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.fork_ev, cudaEventDisableTiming));
                 CU(cudaEventCreateWithFlags(&g.join_ev, cudaEventDisableTiming));
                 for (int i = 0; i < GRAPH_ITERS; ++i)
@@ -901,7 +930,7 @@ ns_status ns_step(ns_ctx *ctx, int n_iters, int *done)
     if (s != NS_OK) return s;
     for (auto &g : ctx->groups) {
         for (int i = 0; i < n_iters; ++i) {
-            s = launch_iteration(ctx, g, ctx->stream, -1, i == 0);
+            s = launch_iteration(ctx, g, ctx->stream, -1, i == 0, i == n_iters - 1);
             if (s != NS_OK) return s;
             ctx->launches += g.launches_per_iter;
         }
@@ -930,12 +959,14 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
         // capture GRAPH_ITERS iterations of this group once; kernels of finished runs return at once
         cudaGraph_t gr;
         CU(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+        g.launches_per_replay = 1;  // the termination test that closes the sequence
         for (int i = 0; i < GRAPH_ITERS; ++i) {
-            s = launch_iteration(ctx, g, g.stream, i, i == 0);
+            s = launch_iteration(ctx, g, g.stream, i, i == 0, i == GRAPH_ITERS - 1);
             if (s != NS_OK) {
                 cudaStreamEndCapture(g.stream, &gr);
                 return s;
             }
+            g.launches_per_replay += g.launches_per_iter;
         }
         s = launch_term_join(ctx, g, g.stream);
         if (s != NS_OK) {
@@ -968,7 +999,7 @@ ns_status ns_run(ns_ctx *ctx, long max_iters)
             CU(cudaGraphLaunch(g.graph, g.stream));
             CU(cudaEventRecord(g.done_ev, g.stream));
             CU(cudaStreamWaitEvent(ctx->stream, g.done_ev, 0));
-            ctx->launches += (long)GRAPH_ITERS * g.launches_per_iter;
+            ctx->launches += g.launches_per_replay;
         }
         done_iters += GRAPH_ITERS;
         s = read_states(ctx, st);
@@ -1275,6 +1306,8 @@ void ns_destroy(ns_ctx *ctx)
         if (g.nz_stream) cudaStreamDestroy(g.nz_stream);
         if (g.nz_fork_ev) cudaEventDestroy(g.nz_fork_ev);
         if (g.nz_join_ev) cudaEventDestroy(g.nz_join_ev);
+        if (g.pick_ev) cudaEventDestroy(g.pick_ev);
+        if (g.tail_ev) cudaEventDestroy(g.tail_ev);
     }
     if (ctx->start_ev) cudaEventDestroy(ctx->start_ev);
     for (auto &rc : ctx->classes)
