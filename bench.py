@@ -41,7 +41,7 @@ DEFAULT_REPLICAS = 17
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per k_hss1 launch from one ncu capture of this workload
 # (profiles/k_hss1_c2x17.md), valid only for the kernel sources with these hashes.
-HSS_TRAFFIC_BYTES = 130.13e6
+HSS_TRAFFIC_BYTES = 130.85e6
 HSS_TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "29d4e8cec9657d33",
                        "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "2215bb2dc5d7ffc3"}
 SMS = 152
