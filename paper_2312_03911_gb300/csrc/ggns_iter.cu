@@ -442,12 +442,13 @@ __device__ void evidence_batch(Stats *st, double *logZ, double *logZ2, int k, co
 }
 
 // ------------------------------------------------------------------------
-// Selection, statistics and spawn of one iteration (Algorithm 3), one CTA per run.
-// dynamic smem: npow2 keys (8 B) | EvScratch
+// Final sweep of a terminated run (Algorithm 3, last loop): every live point is
+// killed in ascending (log L, slot) order and enters the statistics and the dead
+// records.  One CTA per run.  dynamic smem: npow2 keys (8 B) | EvScratch | Stats
 // ------------------------------------------------------------------------
 constexpr int SEL_THREADS = 256;
 
-__device__ void select_body(DevCtx C, int r, bool final_sweep)
+__device__ void final_sweep_body(DevCtx C, int r)
 {
     extern __shared__ unsigned char sraw[];
     const RunDesc &D = C.desc[r];
@@ -464,13 +465,9 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
         for (int i = threadIdx.x; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
     }
     __shared__ int s_abort;
-    __shared__ double s_lx[2];
-    __shared__ int s_cnt[CMAX];
-    __shared__ double s_cum[CMAX];
-    __shared__ int s_start[CMAX];
     const int tid = threadIdx.x;
     const float *logl = C.logl + D.pt_off;
-    const int k = final_sweep ? n : D.k;
+    const int k = n;  // every live point is killed
 
     // ---- ascending (log L, slot) order; NaN first
     for (int i = tid; i < npow; i += blockDim.x)
@@ -509,122 +506,24 @@ __device__ void select_body(DevCtx C, int r, bool final_sweep)
         int4 *dst = reinterpret_cast<int4 *>(C.stats + r);
         for (int i = threadIdx.x; i < (int)(sizeof(Stats) / 16); i += blockDim.x) dst[i] = src[i];
     };
-    // dead records: log L, log prior mass, label (x rows are archived by the walkers)
+    // dead records: log L, log prior mass, label, x
     for (int j = tid; j < k; j += blockDim.x) {
         D.dead_logl[dbase + j] = (float)kL[j];
         D.dead_logw[dbase + j] = E->logw[kP[j]];
         D.dead_label[dbase + j] = kP[j];
-        if (final_sweep) {
-            // the final sweep has no walkers: archive x here
-            const int s = ordr[j];
-            const float *src = C.fa + D.x_off + (long)s * D.d_pad;
-            float *dst = D.dead_x + (dbase + j) * D.d_pad;
-            for (int e = 0; e < D.d_pad; ++e) dst[e] = src[e];
-        }
+        // the final sweep has no walkers: archive x here
+        const int s = ordr[j];
+        const float *src = C.fa + D.x_off + (long)s * D.d_pad;
+        float *dst = D.dead_x + (dbase + j) * D.d_pad;
+        for (int e = 0; e < D.d_pad; ++e) dst[e] = src[e];
     }
     __syncthreads();
-    if (final_sweep) {
-        if (tid == 0) {
-            S->n_dead += k;
-            S->final_done = 1;
-            if (!(S->logz == S->logz)) S->status = NS_ERR_NUMERIC;
-        }
-        store_stats();
-        return;
-    }
     if (tid == 0) {
-        S->lstar = kL[k - 1];
-        // XL statistic on the dead-point sequence: log X (after the kills) + L*
-        double lx = -INFINITY;
-        int na = 0;
-        for (int c = 0; c < CMAX; ++c)
-            if (st->alive[c]) {
-                lx = log_add(lx, st->logXp[c]);
-                ++na;
-            }
-        S->log_xl = lx + kL[k - 1];
-        S->n_clusters = na;
-        s_lx[0] = -INFINITY;
-        for (int c = 0; c < CMAX; ++c)
-            if (st->alive[c]) s_lx[0] = fmax(s_lx[0], st->logXp[c]);
-        // cumulative cluster weights Xbar_p / max Xbar in id order (FP64)
-        double cum = 0.0;
-        for (int c = 0; c < CMAX; ++c) {
-            if (st->alive[c]) cum += exp(st->logXp[c] - s_lx[0]);
-            s_cum[c] = st->alive[c] ? cum : -1.0;
-        }
-        s_lx[1] = cum;
-        // survivors of each cluster occupy [s_start[c], s_start[c] + n_c) in (label, slot) order
-        int off = 0;
-        for (int c = 0; c < CMAX; ++c) {
-            s_start[c] = off;
-            if (st->alive[c]) off += st->n[c];
-            s_cnt[c] = 0;
-        }
-        if (na == 0) {
-            S->status = NS_ERR_NUMERIC;
-            S->done = 1;
-        }
-    }
-    __syncthreads();
-    if (S->done) {
-        store_stats();
-        return;
-    }
-    // ---- survivors sorted by (label, slot)
-    for (int i = tid; i < npow; i += blockDim.x) keys[i] = ~0ull;
-    __syncthreads();
-    for (int j = tid; j < n; j += blockDim.x) {
-        if (j >= k) {
-            const int s = ordr[j];
-            keys[j] = ((unsigned long long)C.label[D.pt_off + s] << 32) | (unsigned)s;
-        }
-    }
-    __syncthreads();
-    block_bitonic_sort(keys, npow);
-    // ---- spawn: cluster ~ Xbar_p, then a uniform surviving member of it
-    const uint32_t iter = (uint32_t)S->iter;
-    for (int j = tid; j < k; j += blockDim.x) {
-        const U4 w = rng_block(D, iter, P_CLUSTER, j, 0, 0);
-        const double target = u01_52(w.x, w.y) * s_lx[1];
-        int chosen = -1, last = -1;
-        for (int c = 0; c < CMAX; ++c) {
-            if (s_cum[c] < 0.0) continue;
-            last = c;
-            if (target < s_cum[c]) {
-                chosen = c;
-                break;
-            }
-        }
-        if (chosen < 0) chosen = last;
-        const int m = st->n[chosen];
-        const U4 w2 = rng_block(D, iter, P_START, j, 0, 0);
-        const int pick = (int)(((unsigned long long)w2.x * (unsigned long long)m) >> 32);
-        const int idx = s_start[chosen] + pick;
-        const unsigned long long kk = (idx < n - k) ? keys[idx] : ~0ull;
-        int slot;
-        if (kk == ~0ull || (int)(kk >> 32) != chosen) {
-            // counts and labels disagree: never expected; record it and fall back to a survivor
-            S->status = NS_ERR_NUMERIC;
-            slot = ordr[k];
-        } else {
-            slot = (int)(kk & 0xffffffffu);
-        }
-        C.start_slot[D.w_off + j] = slot;
-        C.new_label[D.w_off + j] = chosen;
-        atomicAdd(&s_cnt[chosen], 1);
-    }
-    __syncthreads();
-    if (tid < CMAX && st->alive[tid]) st->n[tid] += s_cnt[tid];
-    store_stats();
-    if (tid == 0) {
-        S->wcount[0] = S->wcount[1] = S->wcount[2] = 0;
-        S->t_save = 0;
-        S->t_stop = 0;
-        S->n_in = 0;
-        S->n_out = 0;
         S->n_dead += k;
+        S->final_done = 1;
+        if (!(S->logz == S->logz)) S->status = NS_ERR_NUMERIC;
     }
+    store_stats();
 }
 
 // ------------------------------------------------------------------------
@@ -885,7 +784,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_final(DevCtx C, int r0)
 {
     const int r = r0 + blockIdx.x;
     if (!C.state[r].done || C.state[r].final_done) return;
-    select_body(C, r, true);
+    final_sweep_body(C, r);
 }
 
 size_t sort_smem_bytes(int n_live_max)
@@ -1861,17 +1760,21 @@ __global__ void __launch_bounds__(NOISE_THREADS) k_noise(DevCtx C, const int *ru
     const RunState *S = C.state + r;
     if (S->done) return;
     if (D.d_pad & 3) return;      // drawn in the walk (no whole blocks of four components)
-    const int nb = D.d_pad >> 2;  // blocks of four components
-    const int steps = noise_steps(R.nT, S->t_stop_last);
-    const long items = (long)D.k * steps * nb;
+    const unsigned nb = (unsigned)(D.d_pad >> 2);  // blocks of four components
+    const unsigned steps = (unsigned)noise_steps(R.nT, S->t_stop_last);
+    // item = (walker, step, block); fewer than 2^32 (the noise buffer holds < 2^31 floats).
+    // 32-bit index arithmetic, a shift where the block count is a power of two
+    const unsigned items = (unsigned)D.k * steps * nb;
+    const bool pow2 = (nb & (nb - 1u)) == 0u;
+    const int sh = __ffs((int)nb) - 1;
     const uint32_t iter = (uint32_t)S->iter;
     const long wrow0 = rec_base[r] / R.rec_len;  // first walker row of this run
-    for (long it = (long)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(it % nb);
-        const long ws = it / nb;
-        const int ts = (int)(ws % steps) + 1;
-        const int w = (int)(ws / steps);
-        const U4 wd = rng_block(D, iter, P_NOISE, (uint32_t)w, (uint32_t)ts, (uint32_t)b);
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const unsigned ws = pow2 ? (it >> sh) : it / nb;
+        const unsigned b = it - ws * nb;
+        const unsigned w = ws / steps;
+        const unsigned ts = ws - w * steps + 1u;
+        const U4 wd = rng_block(D, iter, P_NOISE, w, ts, b);
         float4 z;
         box_muller(wd.x, wd.y, z.x, z.y);
         box_muller(wd.z, wd.w, z.z, z.w);
