@@ -708,12 +708,6 @@ __device__ void sort_body(DevCtx C, int r, unsigned char *sraw)
     }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_sort(DevCtx C, int r0)
-{
-    extern __shared__ unsigned char sraw[];
-    sort_body(C, r0 + blockIdx.x, sraw);
-}
-
 // ------------------------------------------------------------------------
 // Appendix H statistics of the iteration's kills (FP64), beside the HSS phases.
 // Reads the kills from the dead records, writes their log prior masses, applies
@@ -1556,12 +1550,6 @@ __device__ void cluster_body(DevCtx C, unsigned long long *lastkey_all, int r, i
     }
 }
 
-__global__ void __launch_bounds__(CL_THREADS) k_cluster(DevCtx C, unsigned long long *lastkey_all, int r0)
-{
-    extern __shared__ int csm[];
-    cluster_body(C, lastkey_all, r0 + blockIdx.x, csm);
-}
-
 // Termination test of the previous iteration, cluster finding and selection of this
 // one, for one run per CTA: one launch instead of three on the iteration's path.
 static_assert(CL_THREADS == SORT_THREADS, "one block shape");
@@ -1724,20 +1712,12 @@ static cudaError_t set_max_smem(const void *fn, size_t smem)
 cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem, size_t sort_smem)
 {
     cudaError_t e;
-    if ((e = set_max_smem((const void *)k_sort, sort_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_evidence, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_final, sel_smem)) != cudaSuccess) return e;
     if ((e = set_max_smem((const void *)k_knn, knn_smem)) != cudaSuccess) return e;
-    if ((e = set_max_smem((const void *)k_term_cluster_sort, cl_smem > sort_smem ? cl_smem : sort_smem)) != cudaSuccess)
-        return e;
-    return set_max_smem((const void *)k_cluster, cl_smem);
+    return set_max_smem((const void *)k_term_cluster_sort, cl_smem > sort_smem ? cl_smem : sort_smem);
 }
 
-cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
-{
-    k_sort<<<n_runs, SORT_THREADS, smem, s>>>(C, r0);
-    return cudaGetLastError();
-}
 cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s)
 {
     k_evidence<<<n_runs, SEL_THREADS, smem, s>>>(C, r0);
@@ -1817,12 +1797,6 @@ cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_
 {
     dim3 grid((max_nlive + 31) / 32, n_runs);
     k_knn<<<grid, KQ_WARPS * 32, smem, s>>>(C, r0);
-    return cudaGetLastError();
-}
-cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
-                           cudaStream_t s)
-{
-    k_cluster<<<n_runs, CL_THREADS, smem, s>>>(C, lastkey, r0);
     return cudaGetLastError();
 }
 constexpr int INFO_BLOCKS = 152;

@@ -22,7 +22,6 @@ size_t evscratch_bytes();
 
 cudaError_t prepare_iteration_kernels(size_t sel_smem, size_t knn_smem, size_t cl_smem, size_t sort_smem);
 // run-range launchers: runs r0 .. r0 + n_runs - 1
-cudaError_t launch_sort(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_evidence(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_final(const DevCtx &C, int r0, int n_runs, size_t smem, cudaStream_t s);
 cudaError_t launch_noise(const DevCtx &C, const int *runs, int nr, int blocks_per_run, const RecView &R,
@@ -34,8 +33,6 @@ cudaError_t launch_term_cluster_sort(const DevCtx &C, int r0, int n_runs, unsign
                                      bool do_term, bool clustering, cudaStream_t s);
 cudaError_t launch_tail(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
 cudaError_t launch_knn(const DevCtx &C, int r0, int n_runs, int max_nlive, size_t smem, cudaStream_t s);
-cudaError_t launch_cluster(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,
-                           cudaStream_t s);
 cudaError_t launch_info(const DevCtx &C, int r, double logz, double *out, cudaStream_t s);
 cudaError_t launch_export(const DevCtx &C, int r, int d, int d_pad, double logz, double *x, double *logp, long n,
                           cudaStream_t s);
