@@ -68,9 +68,10 @@ struct RunClass {
     size_t coop_smem = 0;
 };
 
-// Runs advanced together by one CUDA graph on one stream.  Different groups
-// run on different streams, so one run's selection or HSS phases overlap another
-// run's instead of waiting for the slowest walker of the whole batch.
+// Runs advanced together by one CUDA graph on one stream.  Different groups run
+// on different streams (GGNS_RUNS_PER_GROUP runs each); the default is a single
+// group, because concurrent groups share the SMs and the walkers of one group's
+// single-pass HSS then stop being co-resident.
 struct Group {
     int r0 = 0, nr = 0, max_n = 0;
     std::vector<RunClass> classes;
