@@ -309,7 +309,7 @@ def gpu_arm(args):
             "traffic_unit": "bytes per launch (DRAM read + write)",
             "kernel": ("k_hss1 + k_hss_pick (single pass)" if prof.get("rec_len", 0) > 0 else "k_hss (phases 0-2)"),
             "hss_rec_overflows": prof.get("rec_overflows"), "ops_per_point_step": ops,
-            "noise": ("drawn ahead by k_noise on a second stream (not in this kernel's count): "
+            "noise": ("drawn ahead by k_noise on a side stream (not in this kernel's count): "
                       f"{lane_ops_per_point_step(32, 4, 0.0) - lane_ops_per_point_step(32, 4, 0.0, rng=False):.0f} "
                       "lane-ops per point-step") if drawn_ahead else "drawn in the walk",
             "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
