@@ -25,7 +25,7 @@ _SO = os.path.join(_BUILD, "libggns_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN = 0, 1, 2, 3, 4
+LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN, LIK_TORUS = 0, 1, 2, 3, 4, 5
 P_INIT, P_MOM, P_NOISE, P_RES, P_CLUSTER, P_START, P_PRUNE = 0, 1, 2, 3, 4, 5, 6
 
 
@@ -44,7 +44,8 @@ class LikT(C.Structure):
     _fields_ = [("kind", C.c_int), ("d", C.c_int), ("n_comp", C.c_int),
                 ("means", C.POINTER(C.c_double)), ("log_weights", C.POINTER(C.c_double)),
                 ("sigma", C.POINTER(C.c_double)), ("precision", C.POINTER(C.c_double)),
-                ("rosen_scale", C.c_double)]
+                ("rosen_scale", C.c_double), ("torus_alpha", C.c_double), ("torus_beta", C.c_double),
+                ("torus_c", C.c_double)]
 
 
 class CfgT(C.Structure):
@@ -53,7 +54,7 @@ class CfgT(C.Structure):
                 ("max_ref", C.c_int), ("prune_after", C.c_int), ("termination", C.c_int),
                 ("clustering", C.c_int), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("max_iters", C.c_int), ("noise_mode", C.c_int),
-                ("out_lo", C.c_double), ("out_hi", C.c_double)]
+                ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int)]
 
 
 class BatchStatsT(C.Structure):
@@ -133,7 +134,7 @@ class Likelihood:
     """Holds contiguous FP64 parameter arrays alive for the ctypes struct."""
 
     def __init__(self, kind, d, means=None, sigma=None, log_weights=None, precision=None,
-                 rosen_scale=0.05):
+                 rosen_scale=0.05, torus=None):
         self.kind, self.d = int(kind), int(d)
         self.means = None if means is None else np.ascontiguousarray(np.atleast_2d(means), dtype=np.float64)
         self.n_comp = 1 if self.means is None else self.means.shape[0]
@@ -141,14 +142,16 @@ class Likelihood:
         self.log_weights = None if log_weights is None else np.ascontiguousarray(log_weights, dtype=np.float64)
         self.precision = None if precision is None else np.ascontiguousarray(precision, dtype=np.float64)
         self.rosen_scale = float(rosen_scale)
+        # torus reward (Section 4, eq. torus): (alpha, beta, c)
+        self.torus = (0.0, 0.0, 0.0) if torus is None else tuple(float(v) for v in torus)
         self.struct = LikT(self.kind, self.d, self.n_comp, _dp(self.means), _dp(self.log_weights),
-                           _dp(self.sigma), _dp(self.precision), self.rosen_scale)
+                           _dp(self.sigma), _dp(self.precision), self.rosen_scale, *self.torus)
 
     @classmethod
     def from_spec(cls, spec: dict) -> "Likelihood":
         return cls(spec["kind"], spec["d"], means=spec.get("means"), sigma=spec.get("sigma"),
                    log_weights=spec.get("log_weights"), precision=spec.get("precision"),
-                   rosen_scale=spec.get("rosen_scale", 0.05))
+                   rosen_scale=spec.get("rosen_scale", 0.05), torus=spec.get("torus"))
 
     def logdet(self) -> float:
         if self.precision is None:
@@ -171,7 +174,7 @@ class Likelihood:
 def make_cfg(**kw) -> CfgT:
     c = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.05, tol=0.01, min_ref=1, max_ref=3,
              prune_after=10, termination=0, clustering=0, seed=0, run_id=0, max_iters=100000,
-             noise_mode=0, out_lo=0.05, out_hi=0.15)
+             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0)
     c.update(kw)
     return CfgT(**c)
 

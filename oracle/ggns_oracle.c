@@ -18,7 +18,9 @@
  *   - the evidence definition Z = int L pi dtheta and the importance weights
  *     p_i = L_i w_i / Z (Appendix A);
  *   - the XL-peak termination (Section 3, Appendix I) and the classic
- *     remaining-evidence termination (Algorithm 1).
+ *     remaining-evidence termination (Algorithm 1);
+ *   - the torus reward of Section 4 (eq. torus) on a periodic prior, whose
+ *     normaliser Appendix F gives in closed form.
  * Readings of passages that are ambiguous or garbled are the ones recorded in the
  * design notes of the repository (initial momentum N(0,I); saving inside states
  * once n_ref >= min_ref; per-walker stopping; a size-1 reservoir per walker in
@@ -118,7 +120,8 @@ void orc_normals(uint64_t seed, uint32_t run_id, uint32_t iter, uint32_t purpose
 /* Likelihood families and their gradients (the score, Section 2.3)           */
 /* ------------------------------------------------------------------------- */
 
-enum { ORC_LIK_ISO = 0, ORC_LIK_MIX_ISO = 1, ORC_LIK_DENSE = 2, ORC_LIK_DENSE_MIX = 3, ORC_LIK_ROSEN = 4 };
+enum { ORC_LIK_ISO = 0, ORC_LIK_MIX_ISO = 1, ORC_LIK_DENSE = 2, ORC_LIK_DENSE_MIX = 3, ORC_LIK_ROSEN = 4,
+       ORC_LIK_TORUS = 5 };
 
 typedef struct {
     int kind;
@@ -129,6 +132,7 @@ typedef struct {
     const double *sigma;       /* [n_comp] isotropic standard deviation */
     const double *precision;   /* [d][d], symmetric positive definite   */
     double rosen_scale;        /* multiplies the Rosenbrock sum         */
+    double torus_alpha, torus_beta, torus_c; /* torus reward (Section 4, eq. torus) */
 } orc_lik_t;
 
 /* log det of an SPD matrix by an unpivoted Cholesky factorisation; NAN if not SPD. */
@@ -177,6 +181,24 @@ static double orc_loglik_impl(const orc_lik_t *lk, double logdetP, const double 
             }
         }
         return -lk->rosen_scale * s;
+    }
+    if (lk->kind == ORC_LIK_TORUS) {
+        /* eq. torus: R = (sum over even i of sin(alpha x_i) + sum over odd j of
+         * cos(beta x_j) + c)^3 with the paper's 1-based indices, i.e. sin on the
+         * 0-based odd coordinates and cos on the 0-based even ones; log L = log R =
+         * 3 log(S + c), defined while S + c > 0 (c > d keeps it so everywhere). */
+        double s = lk->torus_c;
+        for (int i = 0; i < d; ++i)
+            s += (i & 1) ? sin(lk->torus_alpha * x[i]) : cos(lk->torus_beta * x[i]);
+        if (!(s > 0.0)) {
+            if (grad) for (int i = 0; i < d; ++i) grad[i] = 0.0;
+            return -INFINITY;
+        }
+        if (grad)
+            for (int i = 0; i < d; ++i)
+                grad[i] = 3.0 / s * ((i & 1) ? lk->torus_alpha * cos(lk->torus_alpha * x[i])
+                                              : -lk->torus_beta * sin(lk->torus_beta * x[i]));
+        return 3.0 * log(s);
     }
     const int K = (lk->kind == ORC_LIK_ISO || lk->kind == ORC_LIK_DENSE) ? 1 : lk->n_comp;
     const int dense = (lk->kind == ORC_LIK_DENSE || lk->kind == ORC_LIK_DENSE_MIX);
@@ -234,6 +256,10 @@ double orc_loglik(const orc_lik_t *lk, const double *x, double *grad)
 void orc_loglik_dmeans(const orc_lik_t *lk, const double *x, double *dmu)
 {
     const int d = lk->d;
+    if (lk->kind == ORC_LIK_TORUS) {
+        for (int i = 0; i < d; ++i) dmu[i] = 0.0; /* no component means */
+        return;
+    }
     const int K = (lk->kind == ORC_LIK_ISO || lk->kind == ORC_LIK_DENSE) ? 1 : lk->n_comp;
     const int dense = (lk->kind == ORC_LIK_DENSE || lk->kind == ORC_LIK_DENSE_MIX);
     const double log2pi = 1.8378770664093454835606594728112;
@@ -290,6 +316,7 @@ typedef struct {
     int max_iters;
     int noise_mode;
     double out_lo, out_hi;
+    int periodic; /* 1: the prior box is a torus, positions wrap instead of reflecting */
 } orc_cfg_t;
 
 typedef struct {
@@ -355,8 +382,15 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
         ++t;
         for (int j = 0; j < n; ++j) {
             double *xj = x + (size_t)j * d, *pj = p + (size_t)j * d;
-            /* x += p dt */
+            /* x += p dt; on a periodic prior the position wraps into [lo, hi) */
             for (int i = 0; i < d; ++i) xj[i] = xj[i] + pj[i] * dt;
+            if (cfg->periodic)
+                for (int i = 0; i < d; ++i) {
+                    const double w = hi[i] - lo[i];
+                    double u = fmod(xj[i] - lo[i], w);
+                    if (u < 0.0) u += w;
+                    xj[i] = lo[i] + u;
+                }
             /* one fused evaluation of log L and its gradient */
             double logl = orc_loglik_impl(lk, logdetP, xj, g);
             int inbox = 1;
