@@ -51,7 +51,8 @@ typedef enum {
     NS_LIK_MIX_ISO = 1,     /* sum_k w_k N(x; mu_k, sigma_k^2 I)                          */
     NS_LIK_DENSE_GAUSS = 2, /* N(x; mu, P^-1) with precision P                            */
     NS_LIK_DENSE_MIX = 3,   /* sum_k w_k N(x; mu_k, P^-1), one precision for all          */
-    NS_LIK_ROSENBROCK = 4   /* -scale * sum_i [100 (x_{i+1} - x_i^2)^2 + (1 - x_i)^2]     */
+    NS_LIK_ROSENBROCK = 4,  /* -scale * sum_i [100 (x_{i+1} - x_i^2)^2 + (1 - x_i)^2]     */
+    NS_LIK_TORUS = 5        /* the torus reward of Section 4, eq. torus (see below)      */
 } ns_lik_kind;
 
 /* Uniform prior on the box [lo_i, hi_i] (the prior pi of Section 2.1). */
@@ -71,6 +72,13 @@ typedef struct {
     const double *sigma;       /* [n_comp] isotropic standard deviations (ISO kinds)     */
     const double *precision;   /* [d][d] row-major symmetric positive definite (DENSE)   */
     double rosen_scale;        /* ROSENBROCK multiplier (1/20 for the benchmark)         */
+    /* TORUS (Section 4, eq. torus; Appendix F): L = (sum of sin(torus_alpha x_i) over the
+     * even 1-based coordinates x_2, x_4, ... + sum of cos(torus_beta x_j) over the odd ones
+     * x_1, x_3, ... + torus_c)^3.  torus_c > d keeps L > 0; integer frequencies make the
+     * normaliser of Appendix F exact.  The prior box of a TORUS run is a torus: a walker
+     * step wraps every coordinate into [lo_i, hi_i) and never leaves the prior.  means,
+     * sigma, precision and log_weights are unused. */
+    double torus_alpha, torus_beta, torus_c;
 } ns_likelihood_spec;
 
 /* Sampler hyper-parameters (Appendix C table; Algorithms 3 and 5). */
@@ -180,7 +188,7 @@ ns_status ns_samples(const ns_ctx *ctx, int run, double *x, double *logp, long c
 /* d log Z / d mu_k for every component mean of run `run`: the posterior-
  * weighted average sum_i p_i d log L(x_i) / d mu_k over the dead points, the
  * weights held fixed (from Z = int L pi, Section 2.1).  grad[n_comp][d];
- * NS_ERR_CAPACITY if cap < n_comp * d; NS_ERR_ARG for ROSENBROCK. */
+ * NS_ERR_CAPACITY if cap < n_comp * d; NS_ERR_ARG for ROSENBROCK and TORUS (no means). */
 ns_status ns_grad_logz(const ns_ctx *ctx, int run, double *grad, long cap);
 
 /* Serialise / restore the complete sampler state (live set, statistics, step
@@ -218,12 +226,13 @@ ns_status ns_lik_forward(const ns_ctx *ctx, const float *x_dev, long n, float *l
  * row-major; copied before return): the parameters theta of the likelihood
  * whose log Z gradient the paper's problem statement asks for (Section 2.1).
  * ns_lik_forward / ns_lik_backward use them at once; sampling uses them after
- * ns_restart.  NS_ERR_ARG for ROSENBROCK (no means).  Synchronises. */
+ * ns_restart.  NS_ERR_ARG for ROSENBROCK and TORUS (no means).  Synchronises. */
 ns_status ns_set_means(ns_ctx *ctx, int run, const double *means_host);
 
 /* Adjoint of ns_lik_forward: given gout_dev[n] = d(loss)/d(log L_i),
  * gx_dev[n][d] = gout_i * d log L_i / dx_i and gmu_dev[n_comp][d] =
- * sum_i gout_i d log L_i / d mu_k (either output may be NULL). */
+ * sum_i gout_i d log L_i / d mu_k (either output may be NULL; gmu_dev must be
+ * NULL for ROSENBROCK and TORUS, which have no means: NS_ERR_ARG otherwise). */
 ns_status ns_lik_backward(const ns_ctx *ctx, const float *x_dev, long n, const float *gout_dev,
                           float *gx_dev, float *gmu_dev, void *stream);
 

@@ -35,6 +35,7 @@ const KindLaunch &kind_launch_mix();
 const KindLaunch &kind_launch_dense();
 const KindLaunch &kind_launch_densemix();
 const KindLaunch &kind_launch_rosen();
+const KindLaunch &kind_launch_torus();
 const KindLaunch &kind_launch(int kind)
 {
     switch (kind) {
@@ -42,6 +43,7 @@ const KindLaunch &kind_launch(int kind)
     case NS_LIK_MIX_ISO: return kind_launch_mix();
     case NS_LIK_DENSE_GAUSS: return kind_launch_dense();
     case NS_LIK_DENSE_MIX: return kind_launch_densemix();
+    case NS_LIK_TORUS: return kind_launch_torus();
     default: return kind_launch_rosen();
     }
 }
@@ -242,6 +244,11 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
     case NS_LIK_ROSENBROCK:
         if (lk.d < 2) return fail(nullptr, NS_ERR_ARG, "ROSENBROCK needs d >= 2");
         break;
+    case NS_LIK_TORUS:
+        if (!(lk.torus_c > 0.0) || !std::isfinite(lk.torus_c) || !std::isfinite(lk.torus_alpha) ||
+            !std::isfinite(lk.torus_beta))
+            return fail(nullptr, NS_ERR_ARG, "TORUS needs finite frequencies and torus_c > 0");
+        break;
     default:
         return fail(nullptr, NS_ERR_ARG, "unknown likelihood kind %d", (int)lk.kind);
     }
@@ -252,7 +259,7 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
 ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int d_pad, std::vector<float> &out,
                        float &lik_const)
 {
-    const int d = b.d, K = (lk.kind == NS_LIK_ROSENBROCK) ? 1 : lk.n_comp;
+    const int d = b.d, K = kind_has_means(lk.kind) ? lk.n_comp : 1;
     const ParLayout L = par_layout(d, d_pad, K, lk.kind);
     out.assign(L.total, 0.f);
     for (int i = 0; i < d; ++i) {
@@ -261,7 +268,7 @@ ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int 
     }
     const double log2pi = 1.8378770664093454836;
     lik_const = 0.f;
-    if (lk.kind == NS_LIK_ROSENBROCK) return NS_OK;
+    if (!kind_has_means(lk.kind)) return NS_OK;
     for (int k = K; k < comp_slots(K, lk.kind); ++k) out[L.comp_b + k] = -INFINITY;  // padding: weight 0
     for (int k = 0; k < K; ++k)
         for (int i = 0; i < d; ++i) out[L.means + (long)k * d_pad + i] = (float)lk.means[(size_t)k * d + i];
@@ -585,7 +592,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         const ns_config &c = cfg[r];
         D.d = box[r].d;
         D.kind = lik[r].kind;
-        D.n_comp = (lik[r].kind == NS_LIK_ROSENBROCK) ? 1 : lik[r].n_comp;
+        D.n_comp = kind_has_means(lik[r].kind) ? lik[r].n_comp : 1;
         int t = env_tile(D.kind, D.d);
         D.tile = (t >= 0) ? t : default_tile(D.kind, D.d);
         const Tile T = tile_of(D.tile);
@@ -603,6 +610,9 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.delta_p = (float)c.delta_p;
         D.keep = (float)std::sqrt(std::max(0.0, 1.0 - c.delta_p * c.delta_p));
         D.rosen_scale = (float)lik[r].rosen_scale;
+        D.torus_a = (float)lik[r].torus_alpha;
+        D.torus_b = (float)lik[r].torus_beta;
+        D.torus_c = (float)lik[r].torus_c;
         D.log_tol = std::log(c.tol);
         D.out_lo = c.out_lo;
         D.out_hi = c.out_hi;
@@ -1159,7 +1169,7 @@ ns_status ns_grad_logz(const ns_ctx *cctx, int run, double *grad, long cap)
     ns_ctx *ctx = const_cast<ns_ctx *>(cctx);
     if (!ctx || run < 0 || run >= ctx->n_runs || !grad) return NS_ERR_ARG;
     const RunDesc &D = ctx->desc[run];
-    if (D.kind == NS_LIK_ROSENBROCK) return fail(ctx, NS_ERR_ARG, "ROSENBROCK has no means");
+    if (!kind_has_means(D.kind)) return fail(ctx, NS_ERR_ARG, "this likelihood kind has no means");
     const int K = D.n_comp;
     if (cap < (long)K * D.d) return fail(ctx, NS_ERR_CAPACITY, "ns_grad_logz: cap < n_comp * d");
     RunState S;
@@ -1374,7 +1384,7 @@ ns_status ns_set_means(ns_ctx *ctx, int run, const double *means_host)
 {
     if (!ctx || !means_host || run < 0 || run >= ctx->n_runs) return NS_ERR_ARG;
     const RunDesc &D = ctx->desc[run];
-    if (D.kind == NS_LIK_ROSENBROCK) return fail(ctx, NS_ERR_ARG, "ROSENBROCK has no means");
+    if (!kind_has_means(D.kind)) return fail(ctx, NS_ERR_ARG, "this likelihood kind has no means");
     const int K = D.n_comp, d = D.d, dp = D.d_pad;
     const ParLayout L = par_layout(d, dp, K, D.kind);
     std::vector<float> m((size_t)K * dp, 0.f);
@@ -1410,7 +1420,7 @@ ns_status ns_lik_backward(const ns_ctx *ctx, const float *x_dev, long n, const f
                           float *gmu_dev, void *stream)
 {
     if (!gout_dev) return NS_ERR_ARG;
-    if (ctx && ctx->desc[0].kind == NS_LIK_ROSENBROCK && gmu_dev) return NS_ERR_ARG;
+    if (ctx && !kind_has_means(ctx->desc[0].kind) && gmu_dev) return NS_ERR_ARG;
     return lik_points(ctx, x_dev, n, 1, nullptr, gx_dev, gout_dev, gmu_dev, stream);
 }
 

@@ -56,6 +56,7 @@ struct RunDesc {
     int d, d_pad, n_live, k, kind, n_comp;
     int n_steps, min_steps, min_ref, max_ref, prune_after, termination, clustering, noise_mode;
     float delta_p, keep, rosen_scale, lik_const;
+    float torus_a, torus_b, torus_c;  // TORUS: sine and cosine frequencies, offset
     double log_tol, out_lo, out_hi, dt_init;
     uint32_t key0, key1;
     long max_iters;
@@ -87,6 +88,12 @@ struct ParLayout {
 // Component slots of the parameter block: an isotropic mixture of up to 8
 // components is padded to 4 or 8 slots (a = 0, b = -inf, mean 0: weight exactly
 // 0), so its likelihood runs over a compile-time count.
+// Kinds without component means (ROSENBROCK, TORUS): one parameter-free component.
+__host__ __device__ inline bool kind_has_means(int kind)
+{
+    return kind != NS_LIK_ROSENBROCK && kind != NS_LIK_TORUS;
+}
+
 __host__ __device__ inline int comp_slots(int n_comp, int kind)
 {
     if (kind == NS_LIK_MIX_ISO && n_comp <= 8) return n_comp <= 4 ? 4 : 8;

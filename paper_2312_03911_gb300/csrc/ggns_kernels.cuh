@@ -14,6 +14,27 @@ struct ParView {
     const float *lo, *hi, *means, *a, *b, *prec, *pmu;
 };
 
+// Periodic prior (TORUS): wrap each real component of x into [lo, hi) after a move,
+// so the walker never leaves the prior (padded components stay at 0).
+template <int KIND, int E>
+__device__ __forceinline__ void wrap_periodic(const RunDesc &D, const ParView &P, float (&x)[E], int c0)
+{
+    if constexpr (KIND == NS_LIK_TORUS) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            if (c < D.d) {
+                const float lo = P.lo[c], w = P.hi[c] - lo;
+                float u = x[e] - lo;
+                u -= w * floorf(u / w);
+                if (u >= w) u -= w;  // rounding of the quotient
+                if (u < 0.f) u = 0.f;
+                x[e] = lo + u;
+            }
+        }
+    }
+}
+
 // Copy the parameter block of run D into shared memory (the precision matrix
 // only when `prec_in_smem`); returns the view.  Call by the whole CTA.
 __device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *sm, bool prec_in_smem)
@@ -277,6 +298,38 @@ __device__ __forceinline__ float lik_eval(const RunDesc &D, const ParView &P, co
         }
         s = gsum<G>(s);
         return -sc * s;
+    } else if constexpr (KIND == NS_LIK_TORUS) {
+        // eq. torus: S = sum of sin(alpha x) over the paper's even (1-based) coordinates, i.e.
+        // the 0-based odd ones, + sum of cos(beta x) over the others + c; log L = 3 log S and
+        // d log L / dx = (3 / S) dS / dx
+        float s = 0.f, ds[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            ds[e] = 0.f;
+            if (c < d) {
+                float sn, cs;
+                if (c & 1) {
+                    sincosf(D.torus_a * x[e], &sn, &cs);
+                    s += sn;
+                    ds[e] = D.torus_a * cs;
+                } else {
+                    sincosf(D.torus_b * x[e], &sn, &cs);
+                    s += cs;
+                    ds[e] = -D.torus_b * sn;
+                }
+            }
+        }
+        s = gsum<G>(s) + D.torus_c;
+        if (!(s > 0.f)) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = 0.f;
+            return -INFINITY;
+        }
+        const float k3 = 3.f / s;
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = k3 * ds[e];
+        return 3.f * logf(s);
     } else {
         // dense kinds: y = P v on CUDA cores, v staged through the walker's shared buffer
         const bool mix = (KIND == NS_LIK_DENSE_MIX);
@@ -632,6 +685,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         const uint32_t res_word = __shfl_sync(0xffffffffu, spare, gbase);
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
+        wrap_periodic<KIND, E>(D, P, x, c0);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
         int outbox = 0;
         float nb[E];
@@ -895,6 +949,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
+        wrap_periodic<KIND, E>(D, P, x, c0);
         float ll;
         if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
@@ -1019,7 +1074,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_lik_points(DevCtx C, int run, c
         float x[E], g[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = (c0 + e < D.d) ? xin[ii * D.d + c0 + e] : 0.f;
-        const bool want_mu = (mode == 1) && gmu != nullptr && KIND != NS_LIK_ROSENBROCK;
+        const bool want_mu = (mode == 1) && gmu != nullptr && kind_has_means(KIND);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, want_mu ? resp : nullptr);
         if (!act) continue;
         if (mode == 0) {

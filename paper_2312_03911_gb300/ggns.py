@@ -19,7 +19,7 @@ NS_OK, NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_TIMEOUT, NS_ERR_STUCK, NS_ERR
     NS_ERR_CAPACITY = range(9)
 STATUS_NAMES = ["NS_OK", "NS_ERR_ARG", "NS_ERR_CUDA", "NS_ERR_OOM", "NS_ERR_TIMEOUT", "NS_ERR_STUCK",
                 "NS_ERR_NUMERIC", "NS_ERR_NOT_DONE", "NS_ERR_CAPACITY"]
-LIK_ISO_GAUSS, LIK_MIX_ISO, LIK_DENSE_GAUSS, LIK_DENSE_MIX, LIK_ROSENBROCK = range(5)
+LIK_ISO_GAUSS, LIK_MIX_ISO, LIK_DENSE_GAUSS, LIK_DENSE_MIX, LIK_ROSENBROCK, LIK_TORUS = range(6)
 
 
 class PriorBox(C.Structure):
@@ -29,7 +29,8 @@ class PriorBox(C.Structure):
 class LikSpec(C.Structure):
     _fields_ = [("kind", C.c_int), ("d", C.c_int), ("n_comp", C.c_int), ("means", C.POINTER(C.c_double)),
                 ("log_weights", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
-                ("precision", C.POINTER(C.c_double)), ("rosen_scale", C.c_double)]
+                ("precision", C.POINTER(C.c_double)), ("rosen_scale", C.c_double),
+                ("torus_alpha", C.c_double), ("torus_beta", C.c_double), ("torus_c", C.c_double)]
 
 
 class Config(C.Structure):
@@ -160,7 +161,8 @@ def _structs(keep: _Keep, spec: dict, lo, hi, cfg: dict):
     n_comp = 1 if means is None else means.shape[0]
     lk = LikSpec(int(spec["kind"]), d, n_comp, _dp(means), _dp(keep.arr(spec.get("log_weights"))),
                  _dp(keep.arr(None if spec.get("sigma") is None else np.atleast_1d(spec["sigma"]))),
-                 _dp(keep.arr(spec.get("precision"))), float(spec.get("rosen_scale", 0.05)))
+                 _dp(keep.arr(spec.get("precision"))), float(spec.get("rosen_scale", 0.05)),
+                 *[float(v) for v in spec.get("torus", (0.0, 0.0, 0.0))])
     c = default_config()
     for k, v in cfg.items():
         if hasattr(c, k) or k in dict(Config._fields_):

@@ -28,7 +28,7 @@ import numpy as np
 
 SEED_BASE = 20231206
 
-LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN = 0, 1, 2, 3, 4
+LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN, LIK_TORUS = 0, 1, 2, 3, 4, 5
 
 # Hyper-parameter defaults: Appendix C table (n_live 200, tol 0.01, min_ref 1,
 # max_ref 3) and dt_ini = 0.1 (Appendix G); the momentum noise is the
@@ -129,9 +129,15 @@ def small_workload(kind: str, d: int, n_live: int, seed: int = 7, **over):
     elif kind == "rosen":
         spec = dict(kind=LIK_ROSEN, d=d, rosen_scale=1.0 / 20.0)
         lo, hi = -2 * np.ones(d), 2 * np.ones(d)
+    elif kind == "torus":
+        # Section 4, eq. torus on the periodic prior [0, 2 pi)^d; c > d keeps L > 0
+        spec = dict(kind=LIK_TORUS, d=d, torus=(1.0, 2.0, d + 1.5))
+        lo, hi = np.zeros(d), np.full(d, 2 * math.pi)
     else:
         raise KeyError(kind)
     cfg = dict(DEFAULT_CFG, n_live=n_live, seed=seed * 1000 + 11, clustering=0)
+    if kind == "torus":
+        cfg["periodic"] = 1  # the oracle's switch; the library takes it from the kind
     cfg.update(over)
     return dict(name=f"{kind}{d}", spec=spec, lo=lo, hi=hi, cfg=cfg)
 
@@ -210,3 +216,13 @@ def truth_logz(w) -> float | None:
     if spec["kind"] in (LIK_DENSE, LIK_DENSE_MIX):
         return -float(np.sum(np.log(np.asarray(hi) - np.asarray(lo))))
     return None
+
+
+def torus_logz(d: int, c: float) -> float:
+    """log Z of the torus reward on the uniform prior over [0, 2 pi)^d (integer frequencies):
+    Appendix F's recursion Z_1 = 2 pi c^3 + 3 pi c, Z_n = 2 pi Z_{n-1} + 3 pi c (2 pi)^(n-1),
+    divided by the prior volume (2 pi)^d."""
+    z = 2 * math.pi * c**3 + 3 * math.pi * c
+    for m in range(2, d + 1):
+        z = 2 * math.pi * z + 3 * math.pi * c * (2 * math.pi) ** (m - 1)
+    return math.log(z) - d * math.log(2 * math.pi)

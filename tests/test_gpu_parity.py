@@ -134,7 +134,8 @@ def test_evidence_statistics_match_sequential_update(seed, counts, k):
 
 # ---------------------------------------------------------------- likelihoods
 @pytest.mark.parametrize("kind,d", [("iso", 2), ("iso", 33), ("mix", 32), ("mix", 7), ("dense", 20),
-                                    ("dense_mix", 24), ("rosen", 9), ("rosen", 2), ("mix", 130)])
+                                    ("dense_mix", 24), ("rosen", 9), ("rosen", 2), ("mix", 130),
+                                    ("torus", 6), ("torus", 33)])
 def test_likelihood_and_score_match_oracle(kind, d):
     w = W.small_workload(kind, d, 20, seed=d)
     s = ggns.Sampler([w])
@@ -181,7 +182,7 @@ def _ball_start(d, n, R, rng):
 
 
 @pytest.mark.parametrize("kind,d,noise_mode", [("iso", 8, 1), ("iso", 8, 0), ("mix", 32, 1), ("iso", 2, 1),
-                                               ("rosen", 6, 1), ("dense", 16, 1)])
+                                               ("rosen", 6, 1), ("dense", 16, 1), ("torus", 6, 1)])
 def test_hss_trajectories_match_oracle(kind, d, noise_mode):
     """At most 20 steps from identical FP32 inputs: identical inside/outside decisions, step counts
     and reservoir picks, and outputs within 1e-5 relative.  Inputs whose oracle trajectory comes
@@ -193,6 +194,8 @@ def test_hss_trajectories_match_oracle(kind, d, noise_mode):
     center = np.zeros(d) if kind != "mix" else w["spec"]["means"][0]
     if kind == "rosen":
         center = np.full(d, 0.3)
+    if kind == "torus":
+        center = np.full(d, 0.2)  # near the seam at 0 = 2 pi: walks cross it and wrap
     found = False
     for attempt in range(40):
         x0 = (center + _ball_start(d, n, 0.15, rng)).astype(np.float32).astype(np.float64)
@@ -243,6 +246,26 @@ def test_c1_evidence_against_closed_form_and_oracle():
                    for r in range(R)])
     se = math.sqrt(z.var() / R + zo.var() / R)
     assert abs(z.mean() - zo.mean()) < max(0.2, 3 * se)
+
+
+def test_torus_evidence_against_the_normaliser():
+    """The torus reward of Section 4 on its periodic prior: the batch's mean log Z against
+    Appendix F's closed form, and against the oracle's runs of the same workload."""
+    d = 4
+    w = W.small_workload("torus", d, 200, seed=5)
+    w = dict(w, cfg=dict(w["cfg"], termination=1, tol=1e-3, noise_mode=1, delta_p=0.2))
+    runs = [dict(w, cfg=dict(w["cfg"], run_id=r)) for r in range(16)]
+    _, res = _run_gpu(runs)
+    assert all(r["status"] == 0 and r["terminated"] == 1 for r in res)
+    truth = W.torus_logz(d, w["spec"]["torus"][2])
+    z = np.array([r["logz"] for r in res])
+    err = float(np.mean([r["logz_err"] for r in res])) / math.sqrt(len(z))
+    assert abs(z.mean() - truth) < 4 * err + 0.02
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    zo = np.array([oracle.run(lik, w["lo"], w["hi"], oracle.make_cfg(**dict(w["cfg"], run_id=r)))["logz"]
+                   for r in range(8)])
+    se = math.hypot(z.std() / math.sqrt(len(z)), zo.std() / math.sqrt(len(zo)))
+    assert abs(z.mean() - zo.mean()) < 4 * se + 0.02
 
 
 def test_batch_of_uneven_runs_and_posterior():
