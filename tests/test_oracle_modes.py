@@ -1,0 +1,42 @@
+"""Mode finding with the cluster recognition of Algorithm 4 (Sec. 3, mode collapse; App. G's
+multimodal tests): a 2-D mixture of nine well separated Gaussians on a 3 x 3 grid."""
+import math
+
+import numpy as np
+
+import oracle
+from paper_2312_03911_gb300 import workloads as W
+
+GRID = np.array([[a, b] for a in (-0.6, 0.0, 0.6) for b in (-0.6, 0.0, 0.6)])
+SIG = 0.05
+
+
+def _runs(clustering, n_runs=10):
+    lik = oracle.Likelihood(W.LIK_MIX_ISO, 2, means=GRID, sigma=np.full(9, SIG), log_weights=np.full(9, -math.log(9)))
+    out = []
+    for r in range(n_runs):
+        cfg = oracle.make_cfg(n_live=300, n_steps=1000, dt_init=0.1, delta_p=0.2, noise_mode=1, tol=1e-3,
+                              termination=1, clustering=clustering, seed=77, run_id=r)
+        out.append(oracle.run(lik, -np.ones(2), np.ones(2), cfg))
+    return out
+
+
+def _modes_found(o):
+    """Modes holding at least a quarter of their share (1/9) of the posterior mass within 3 sigma."""
+    lw = o["dead_logw"] + o["dead_logl"] - o["logz"]
+    p = np.exp(lw - lw.max())
+    p /= p.sum()
+    near = np.linalg.norm(o["dead_x"][:, None, :] - GRID[None], axis=2) < 3 * SIG
+    mass = np.array([p[near[:, k]].sum() for k in range(len(GRID))])
+    return int((mass > 0.25 / len(GRID)).sum())
+
+
+def test_clustering_finds_every_mode_and_the_evidence():
+    runs = _runs(clustering=1)
+    assert all(o["status"] == 0 and o["terminated"] == 1 for o in runs)
+    assert [_modes_found(o) for o in runs] == [9] * len(runs)
+    assert max(o["max_clusters"] for o in runs) >= 9  # the clusters were recognised, not only sampled
+    # normalised components well inside the box [-1, 1]^2: Z = 1 / 4
+    z = np.array([o["logz"] for o in runs])
+    err = float(np.mean([o["logz_err"] for o in runs])) / math.sqrt(len(z))
+    assert abs(z.mean() - math.log(0.25)) < 4 * err
