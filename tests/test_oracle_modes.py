@@ -40,3 +40,23 @@ def test_clustering_finds_every_mode_and_the_evidence():
     z = np.array([o["logz"] for o in runs])
     err = float(np.mean([o["logz_err"] for o in runs])) / math.sqrt(len(z))
     assert abs(z.mean() - math.log(0.25)) < 4 * err
+
+
+def test_modes_found_grow_with_n_live_as_in_the_ablation_table():
+    """The ablation table of App. G counts the modes found on a nine-Gaussian mixture for
+    n_live = 20, 50, 100, 200 (with mode collapse mitigation: 4.1, 6.4, 8.4, 9).  Its mixture's
+    parameters are not printed; on the grid here the count must likewise grow with n_live from
+    about four to nearly all nine."""
+    lik = oracle.Likelihood(W.LIK_MIX_ISO, 2, means=GRID, sigma=np.full(9, SIG), log_weights=np.full(9, -math.log(9)))
+    means = []
+    for n_live in (20, 50, 100, 200):
+        found = []
+        for r in range(10):
+            cfg = oracle.make_cfg(n_live=n_live, n_steps=1000, dt_init=0.1, delta_p=0.2, noise_mode=1, tol=1e-3,
+                                  termination=1, clustering=1, seed=91, run_id=r)
+            o = oracle.run(lik, -np.ones(2), np.ones(2), cfg)
+            assert o["status"] == 0
+            found.append(_modes_found(o))
+        means.append(float(np.mean(found)))
+    assert all(b >= a for a, b in zip(means, means[1:])), means
+    assert 2.5 <= means[0] <= 5.5 and means[-1] >= 8.5, means
