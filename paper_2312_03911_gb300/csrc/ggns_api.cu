@@ -1266,6 +1266,7 @@ ns_status ns_state_load(ns_ctx *ctx, const void *buf, size_t n)
     };
     ns_status s;
     std::vector<RunState> st(ctx->n_runs);
+    if (p + sizeof(RunState) * ctx->n_runs > end) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
     memcpy(st.data(), p, sizeof(RunState) * ctx->n_runs);
     if ((s = h2d(ctx->state_dev, sizeof(RunState) * ctx->n_runs)) != NS_OK) return s;
     if ((s = h2d(ctx->stats_dev, sizeof(Stats) * ctx->n_runs)) != NS_OK) return s;
@@ -1280,6 +1281,8 @@ ns_status ns_state_load(ns_ctx *ctx, const void *buf, size_t n)
         if (p + sizeof nd > end) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
         memcpy(&nd, p, sizeof nd);
         p += sizeof nd;
+        if (nd < 0 || nd > (long)((end - p) / sizeof(float)))
+            return fail(ctx, NS_ERR_ARG, "ns_state_load: bad dead-point count");
         if (nd + ctx->desc[r].n_live + (long)GRAPH_ITERS * ctx->desc[r].k > ctx->desc[r].dead_cap) {
             // grow this run's arena before copying its rows in
             RunState zero = st[r];
