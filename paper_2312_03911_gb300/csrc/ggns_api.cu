@@ -166,6 +166,23 @@ ns_status fail(ns_ctx *c, ns_status st, const char *fmt, ...)
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
     } while (0)
 
+// Device scratch of one call, freed when the call returns on every path.
+struct DevScratch {
+    void *p = nullptr;
+    DevScratch() = default;
+    DevScratch(const DevScratch &) = delete;
+    DevScratch &operator=(const DevScratch &) = delete;
+    ~DevScratch()
+    {
+        if (p) cudaFree(p);
+    }
+    template <typename T>
+    T *as() const
+    {
+        return static_cast<T *>(p);
+    }
+};
+
 int default_tile(int kind, int d)
 {
     (void)kind;
@@ -1152,15 +1169,13 @@ ns_status ns_samples(const ns_ctx *cctx, int run, double *x, double *logp, long 
     if (cap < S.n_dead) return fail(ctx, NS_ERR_CAPACITY, "ns_samples: cap %ld < %ld dead points", cap, S.n_dead);
     const RunDesc &D = ctx->desc[run];
     const long n = S.n_dead;
-    double *xd = nullptr, *ld = nullptr;
-    if (x) CU(cudaMalloc(&xd, sizeof(double) * (size_t)n * D.d));
-    if (logp) CU(cudaMalloc(&ld, sizeof(double) * (size_t)n));
-    CU(launch_export(ctx->dc, run, D.d, D.d_pad, S.logz, xd, ld, n, ctx->stream));
-    if (x) CU(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)n * D.d, cudaMemcpyDeviceToHost, ctx->stream));
-    if (logp) CU(cudaMemcpyAsync(logp, ld, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    DevScratch xs, ls;
+    if (x) CU(cudaMalloc(&xs.p, sizeof(double) * (size_t)n * D.d));
+    if (logp) CU(cudaMalloc(&ls.p, sizeof(double) * (size_t)n));
+    CU(launch_export(ctx->dc, run, D.d, D.d_pad, S.logz, xs.as<double>(), ls.as<double>(), n, ctx->stream));
+    if (x) CU(cudaMemcpyAsync(x, xs.p, sizeof(double) * (size_t)n * D.d, cudaMemcpyDeviceToHost, ctx->stream));
+    if (logp) CU(cudaMemcpyAsync(logp, ls.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (xd) cudaFree(xd);
-    if (ld) cudaFree(ld);
     return NS_OK;
 }
 
@@ -1453,6 +1468,21 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
     double *dw = nullptr;
     RunDesc *ddesc = nullptr;
     RunState *dstate = nullptr;
+    RecView R{};
+    long *rbase = nullptr;
+    // every scratch buffer of this call is freed when it returns, on every path
+    struct FreeAtExit {
+        std::vector<void **> slots;
+        ~FreeAtExit()
+        {
+            for (void **q : slots)
+                if (*q) cudaFree(*q);
+        }
+    } scratch;
+    scratch.slots = {(void **)&fa,    (void **)&logl,  (void **)&lab,    (void **)&order,  (void **)&start,
+                     (void **)&nlab,  (void **)&wint,  (void **)&wres,   (void **)&dx,     (void **)&dl,
+                     (void **)&dw,    (void **)&dlab,  (void **)&runs,   (void **)&ddesc,  (void **)&dstate,
+                     (void **)&R.meta, (void **)&R.ll, (void **)&R.x,    (void **)&rbase};
     CU(cudaMalloc(&fa, sizeof(float) * fa_len));
     CU(cudaMalloc(&logl, sizeof(float) * 2 * n));
     CU(cudaMalloc(&lab, sizeof(int) * 2 * n));
@@ -1518,8 +1548,6 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
             if (r == 0) cls = i;
     const RunClass &rc = ctx->classes[cls];
     // the single-pass form where the context uses it and all n walkers are resident
-    RecView R{};
-    long *rbase = nullptr;
     int single = 0;
     if (ctx->rec.rec_len > 0) {
         int per_sm = 0, n_sm = 0;
@@ -1559,9 +1587,6 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         stats_host[2] = S.t_save;
         stats_host[3] = S.t_stop;
     }
-    void *ptrs[] = {fa, logl, lab, order, start, nlab, wint, wres, dx, dl, dw, dlab, runs, ddesc, dstate,
-                    R.meta, R.ll, R.x, rbase};
-    for (void *p : ptrs) cudaFree(p);
     return NS_OK;
 }
 
@@ -1570,27 +1595,22 @@ ns_status ns_knn_components(const float *x_dev, int m, int d, int *comp_dev, int
     ns_ctx *ctx = nullptr;
     if (m < 1 || m > NLIVE_MAX || d < 1 || d > DMAX || !x_dev || !comp_dev) return NS_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int *label, *csize, *nbr, *nc;
-    unsigned long long *lk;
-    CU(cudaMalloc(&label, sizeof(int) * m));
-    CU(cudaMalloc(&csize, sizeof(int) * CMAX));
-    CU(cudaMalloc(&nbr, sizeof(int) * (size_t)m * KNN_K));
-    CU(cudaMalloc(&nc, sizeof(int)));
-    CU(cudaMalloc(&lk, sizeof(unsigned long long) * m));
+    DevScratch label, csize, nbr, nc, lk;
+    CU(cudaMalloc(&label.p, sizeof(int) * m));
+    CU(cudaMalloc(&csize.p, sizeof(int) * CMAX));
+    CU(cudaMalloc(&nbr.p, sizeof(int) * (size_t)m * KNN_K));
+    CU(cudaMalloc(&nc.p, sizeof(int)));
+    CU(cudaMalloc(&lk.p, sizeof(unsigned long long) * m));
     std::vector<int> cs(CMAX, 0);
     cs[0] = m;
-    CU(cudaMemsetAsync(label, 0, sizeof(int) * m, s));
-    CU(cudaMemcpyAsync(csize, cs.data(), sizeof(int) * CMAX, cudaMemcpyHostToDevice, s));
-    CU(launch_knn_components(x_dev, m, d, label, csize, nbr, comp_dev, lk, nc, s));
+    CU(cudaMemsetAsync(label.p, 0, sizeof(int) * m, s));
+    CU(cudaMemcpyAsync(csize.p, cs.data(), sizeof(int) * CMAX, cudaMemcpyHostToDevice, s));
+    CU(launch_knn_components(x_dev, m, d, label.as<int>(), csize.as<int>(), nbr.as<int>(), comp_dev,
+                             lk.as<unsigned long long>(), nc.as<int>(), s));
     int h = 0;
-    CU(cudaMemcpyAsync(&h, nc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(&h, nc.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (n_comp_host) *n_comp_host = h;
-    cudaFree(label);
-    cudaFree(csize);
-    cudaFree(nbr);
-    cudaFree(nc);
-    cudaFree(lk);
     return NS_OK;
 }
 
@@ -1631,25 +1651,24 @@ ns_status ns_stats_update(int n_clusters, const int *counts, const double *logx0
         if (labels[j] < 0 || labels[j] >= n_clusters || --left[labels[j]] < 0)
             return fail(nullptr, NS_ERR_ARG, "ns_stats_update: more kills than live points in a cluster");
     }
-    Stats *dst;
-    double *zz, *kL, *lw;
-    int *kP;
-    CU(cudaMalloc(&dst, sizeof(Stats)));
-    CU(cudaMalloc(&zz, 2 * sizeof(double)));
-    CU(cudaMalloc(&kL, sizeof(double) * k));
-    CU(cudaMalloc(&kP, sizeof(int) * k));
-    CU(cudaMalloc(&lw, sizeof(double) * k));
+    DevScratch dst, zz, kL, kP, lw;
+    CU(cudaMalloc(&dst.p, sizeof(Stats)));
+    CU(cudaMalloc(&zz.p, 2 * sizeof(double)));
+    CU(cudaMalloc(&kL.p, sizeof(double) * k));
+    CU(cudaMalloc(&kP.p, sizeof(int) * k));
+    CU(cudaMalloc(&lw.p, sizeof(double) * k));
     const double z0[2] = {-INFINITY, -INFINITY};
-    CU(cudaMemcpy(dst, &T, sizeof T, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(zz, z0, sizeof z0, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(kL, logl, sizeof(double) * k, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(kP, labels, sizeof(int) * k, cudaMemcpyHostToDevice));
-    CU(launch_stats_plain(dst, zz, k, kL, kP, lw, nullptr));
+    CU(cudaMemcpy(dst.p, &T, sizeof T, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(zz.p, z0, sizeof z0, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(kL.p, logl, sizeof(double) * k, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(kP.p, labels, sizeof(int) * k, cudaMemcpyHostToDevice));
+    CU(launch_stats_plain(dst.as<Stats>(), zz.as<double>(), k, kL.as<double>(), kP.as<int>(), lw.as<double>(),
+                          nullptr));
     CU(cudaDeviceSynchronize());
     Stats R;
     double zr[2];
-    CU(cudaMemcpy(&R, dst, sizeof R, cudaMemcpyDeviceToHost));
-    CU(cudaMemcpy(zr, zz, sizeof zr, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&R, dst.p, sizeof R, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(zr, zz.p, sizeof zr, cudaMemcpyDeviceToHost));
     out[0] = zr[0];
     out[1] = zr[1];
     out[2] = 0.0;
@@ -1658,12 +1677,7 @@ ns_status ns_stats_update(int n_clusters, const int *counts, const double *logx0
         out[3 + 3 * c + 1] = R.logXp2[c];
         out[3 + 3 * c + 2] = R.logZXp[c];
     }
-    CU(cudaMemcpy(out + 3 + 3 * n_clusters, lw, sizeof(double) * k, cudaMemcpyDeviceToHost));
-    cudaFree(dst);
-    cudaFree(zz);
-    cudaFree(kL);
-    cudaFree(kP);
-    cudaFree(lw);
+    CU(cudaMemcpy(out + 3 + 3 * n_clusters, lw.p, sizeof(double) * k, cudaMemcpyDeviceToHost));
     return NS_OK;
 }
 
