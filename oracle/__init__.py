@@ -54,7 +54,7 @@ class CfgT(C.Structure):
                 ("max_ref", C.c_int), ("prune_after", C.c_int), ("termination", C.c_int),
                 ("clustering", C.c_int), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("max_iters", C.c_int), ("noise_mode", C.c_int),
-                ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int)]
+                ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int), ("keep_last", C.c_int)]
 
 
 class BatchStatsT(C.Structure):
@@ -174,7 +174,7 @@ class Likelihood:
 def make_cfg(**kw) -> CfgT:
     c = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.05, tol=0.01, min_ref=1, max_ref=3,
              prune_after=10, termination=0, clustering=0, seed=0, run_id=0, max_iters=100000,
-             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0)
+             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0)
     c.update(kw)
     return CfgT(**c)
 

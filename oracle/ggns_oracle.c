@@ -317,6 +317,7 @@ typedef struct {
     int noise_mode;
     double out_lo, out_hi;
     int periodic; /* 1: the prior box is a torus, positions wrap instead of reflecting */
+    int keep_last; /* 1: return the last saved state instead of a uniform one (App. G ablation) */
 } orc_cfg_t;
 
 typedef struct {
@@ -457,7 +458,9 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
                 uint32_t w[4];
                 orc_rng_block(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, 0, w);
                 uint32_t word = (w[0] & 511u) | ((w[1] & 511u) << 9) | ((w[2] & 511u) << 18) | ((w[3] & 31u) << 27);
-                if ((((uint64_t)word * (uint64_t)count[j]) >> 32) == 0) {
+                /* keep_last: the App. G ablation that integrates a fixed number of steps and
+                 * keeps the last sample, in place of the size-1 reservoir */
+                if (cfg->keep_last || (((uint64_t)word * (uint64_t)count[j]) >> 32) == 0) {
                     memcpy(xr + (size_t)j * d, x + (size_t)j * d, sizeof(double) * d);
                     lr[j] = logl_now[j];
                 }

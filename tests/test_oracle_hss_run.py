@@ -154,3 +154,26 @@ def test_grad_logz_statistically_matches_the_truncation_effect():
     gs = np.array(gs)
     se = gs.std(0) / math.sqrt(len(gs)) + 1e-3
     assert np.all(np.abs(gs.mean(0) - truth) < 4 * se), (gs.mean(0), truth, se)
+
+
+def test_keep_last_returns_the_last_inside_state():
+    """The App. G ablation: a fixed number of steps (min_steps = n_steps, saving from the first
+    step) and the last inside state kept, instead of a uniform pick over the saved states."""
+    d = 4
+    lik, lstar = _ball_case(d, R=0.3)
+    rng = np.random.default_rng(2)
+    v = rng.standard_normal((32, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    x0 = v * 0.3 * rng.uniform(size=(32, 1)) ** (1.0 / d)
+    cfg = oracle.make_cfg(seed=9, noise_mode=1, delta_p=0.2, min_ref=0, max_ref=10**6, n_steps=20, min_steps=20,
+                          prune_after=0, keep_last=1)
+    o = oracle.hss_batch(lik, -np.ones(d), np.ones(d), cfg, 0, x0, [lik.loglik(q) for q in x0], lstar, 0.05,
+                         trace=True)
+    tr = o["trace"]
+    assert tr.shape[0] == 20
+    for j in range(len(x0)):
+        inside = np.nonzero(tr[:, j, 2 * d + 1] == 0)[0]
+        if len(inside):
+            np.testing.assert_array_equal(o["x"][j], tr[inside[-1], j, :d])
+        else:
+            np.testing.assert_array_equal(o["x"][j], x0[j])
