@@ -4,6 +4,11 @@ Argument marshalling only: every step of the sampler runs in the CUDA library.
 The library is loaded on first use from ``paper_2312_03911_gb300/_build`` and
 this module raises if it is missing or if no CUDA device is present; there is
 no CPU fallback.
+
+A run is a dict ``{spec, lo, hi, cfg}``: ``spec`` holds ``kind`` (LIK_*), ``d`` and the
+parameters of that kind (``means`` [n_comp][d], ``sigma``, ``log_weights``, ``precision``
+[d][d], ``rosen_scale``, ``torus`` = (alpha, beta, c)); ``lo``/``hi`` bound the uniform
+prior (a torus for LIK_TORUS); ``cfg`` overrides fields of ``ns_config`` by name.
 """
 from __future__ import annotations
 
