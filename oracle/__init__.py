@@ -6,8 +6,8 @@ leg of ``bench.py`` may import this package; the product library never does.
 The arithmetic lives in ``ggns_oracle.c`` (plain C, FP64, single-threaded); this
 module compiles it with gcc and wraps it with ctypes.  It shares no code with the
 CUDA path.  Every function cites the passage of the paper it follows in the C
-source; the readings taken where the paper is ambiguous are listed in the design
-notes of the repository.
+source; the readings taken where the paper is ambiguous are stated in the header of
+``ggns_oracle.c``.
 """
 from __future__ import annotations
 
@@ -54,7 +54,9 @@ class CfgT(C.Structure):
                 ("max_ref", C.c_int), ("prune_after", C.c_int), ("termination", C.c_int),
                 ("clustering", C.c_int), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("max_iters", C.c_int), ("noise_mode", C.c_int),
-                ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int), ("keep_last", C.c_int)]
+                ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int), ("keep_last", C.c_int),
+                ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int),
+                ("box_fold", C.c_int)]
 
 
 class BatchStatsT(C.Structure):
@@ -65,7 +67,8 @@ class BatchStatsT(C.Structure):
 class ResultT(C.Structure):
     _fields_ = [("logz", C.c_double), ("logz_err", C.c_double), ("logz_skilling_err", C.c_double),
                 ("info_h", C.c_double), ("n_iter", C.c_long), ("n_dead", C.c_long),
-                ("n_like", C.c_long), ("n_steps_total", C.c_long), ("n_fallback", C.c_long), ("dt", C.c_double),
+                ("n_like", C.c_long), ("n_steps_total", C.c_long), ("n_fallback", C.c_long),
+                ("n_region_rejected", C.c_long), ("dt", C.c_double),
                 ("n_clusters_final", C.c_int), ("max_clusters", C.c_int),
                 ("terminated", C.c_int), ("status", C.c_int)]
 
@@ -119,6 +122,9 @@ def lib():
                                   C.POINTER(LikT), C.POINTER(ResultT), C.c_long, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int),
                                   C.POINTER(IterTraceT)]
+            L.orc_territory.restype = C.c_int
+            L.orc_territory.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), C.c_int,
+                                        C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_int)]
             L.orc_grad_logz_means.argtypes = [C.POINTER(LikT), C.c_long, C.POINTER(C.c_double),
                                               C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double,
                                               C.POINTER(C.c_double)]
@@ -174,7 +180,7 @@ class Likelihood:
 def make_cfg(**kw) -> CfgT:
     c = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.05, tol=0.01, min_ref=1, max_ref=3,
              prune_after=10, termination=0, clustering=0, seed=0, run_id=0, max_iters=100000,
-             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0)
+             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0, noise_inside=0, pick_all=0, territory=0, box_fold=0)
     c.update(kw)
     return CfgT(**c)
 
@@ -286,13 +292,26 @@ def run(lik: Likelihood, lo, hi, cfg: CfgT, dead_cap=None, trace=False):
     n = res.n_dead
     out = dict(logz=res.logz, logz_err=res.logz_err, logz_skilling_err=res.logz_skilling_err,
                info_h=res.info_h, n_iter=res.n_iter, n_dead=n, n_like=res.n_like,
-               n_steps_total=res.n_steps_total, n_fallback=res.n_fallback, dt=res.dt, n_clusters_final=res.n_clusters_final,
+               n_steps_total=res.n_steps_total, n_fallback=res.n_fallback,
+               n_region_rejected=res.n_region_rejected, dt=res.dt, n_clusters_final=res.n_clusters_final,
                max_clusters=res.max_clusters, terminated=res.terminated, status=res.status,
                dead_x=dx[:n], dead_logl=dl[:n], dead_logw=dw[:n], dead_label=dlab[:n])
     if trace:
         it = res.n_iter
         out["trace"] = {f: np.array([getattr(tr[i], f) for i in range(it)]) for f, _ in IterTraceT._fields_}
     return out
+
+
+def territory(surv, surv_label, xn, want):
+    """Which new points stay in the region of the cluster they were spawned in (1) or are rejected (0)."""
+    surv = np.ascontiguousarray(surv, dtype=np.float32)
+    xn = np.ascontiguousarray(xn, dtype=np.float32)
+    sl = np.ascontiguousarray(surv_label, dtype=np.int32)
+    wl = np.ascontiguousarray(want, dtype=np.int32)
+    keep = np.zeros(len(xn), dtype=np.int32)
+    lib().orc_territory(len(surv), surv.shape[1], surv.ctypes.data_as(C.POINTER(C.c_float)), _ip(sl), len(xn),
+                        xn.ctypes.data_as(C.POINTER(C.c_float)), _ip(wl), _ip(keep))
+    return keep
 
 
 def grad_logz_means(lik: Likelihood, xs, logl, logw, logz):

@@ -21,13 +21,25 @@
  *     remaining-evidence termination (Algorithm 1);
  *   - the torus reward of Section 4 (eq. torus) on a periodic prior, whose
  *     normaliser Appendix F gives in closed form.
- * Readings of passages that are ambiguous or garbled are the ones recorded in the
- * design notes of the repository (initial momentum N(0,I); saving inside states
- * once n_ref >= min_ref; per-walker stopping; a size-1 reservoir per walker in
- * place of the pooled archive; strict inequality L > L*; update6 read as
- * ZX_q -> ZX_q + X_pX_q L/(n_p+1); the final sweep with decreasing n_p; the
- * XL-peak statistic taken on the dead-point sequence, L_i X_i, as the
- * hyper-parameter table of Appendix C defines it).
+ * Readings of passages that are ambiguous or garbled: the initial momentum is
+ * N(0, I); states are saved once every walker has reflected min_ref times and the
+ * loop runs until every walker has reflected max_ref times (the global loop
+ * condition of Algorithm 5); the momentum noise perturbs inside steps only and an
+ * outside step only reflects (Section 2.3: a particle left behind the boundary
+ * gets stuck); each walker returns one state drawn uniformly over the steps of the
+ * saving window, and a drawn outside step is rejected, so the walker returns its
+ * start point (the rejection of slice sampling, Section 2.3); with more than one
+ * cluster alive, a new point whose nearest surviving point belongs to another
+ * cluster is rejected the same way (a cluster's new points stay in its region);
+ * the prior box reflects a walker exactly (the position folds back across the
+ * face and the momentum component flips), so, as in Algorithm 5, only the
+ * iso-likelihood boundary makes a step an outside step;
+ * strict inequality L > L*; update6 read as ZX_q -> ZX_q + X_pX_q L/(n_p+1);
+ * the final sweep with decreasing n_p; the XL-peak statistic taken on the
+ * dead-point sequence, L_i X_i, as the hyper-parameter table of Appendix C
+ * defines it.  The printed forms (noise on every step, the pick among saved
+ * inside states only, no region check, the box as an outside region) remain
+ * switches of orc_cfg_t.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), written here from its published
@@ -318,6 +330,14 @@ typedef struct {
     double out_lo, out_hi;
     int periodic; /* 1: the prior box is a torus, positions wrap instead of reflecting */
     int keep_last; /* 1: return the last saved state instead of a uniform one (App. G ablation) */
+    int noise_inside; /* 1: the momentum noise perturbs inside steps only; an outside step only reflects */
+    int pick_all;     /* 1: the pick is uniform over every step of the saving window and an outside
+                         step returns the start point (rejection); 0: uniform over saved inside states */
+    int territory;    /* 1: with several clusters alive, a new point whose nearest surviving point
+                         belongs to another cluster is rejected (the walker returns its start point) */
+    int box_fold;     /* 1: the prior box reflects a walker exactly (the position folds back across
+                         the face and the momentum component flips; not an outside step); 0: leaving
+                         the box is an outside step that reflects off the violated faces */
 } orc_cfg_t;
 
 typedef struct {
@@ -343,7 +363,10 @@ typedef struct {
  *     min_steps, at most n_steps steps).
  * Each walker returns one state drawn uniformly from its own saved inside states
  * (a size-1 reservoir; replacement with probability 1/count), or its start point
- * if it saved none.  Walkers that stay outside for prune_after consecutive steps
+ * if it saved none.  With pick_all the reservoir runs over every step of the
+ * saving window, inside or outside, and a drawn outside step is a rejection: the
+ * walker returns its start point.  With noise_inside an outside step reflects
+ * and takes no noise.  Walkers that stay outside for prune_after consecutive steps
  * are reset to their start point with a fresh momentum (Section 3, pruning).
  * Random numbers: walker j uses slot j of iteration `iter`.
  * If trace != NULL it receives, per step t and walker j, x then p then logL and
@@ -392,6 +415,17 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
                     if (u < 0.0) u += w;
                     xj[i] = lo[i] + u;
                 }
+            else if (cfg->box_fold)
+                for (int i = 0; i < d; ++i) {
+                    /* specular reflection off the faces lo_i, hi_i: the path unfolded on a
+                     * line of period 2w folds back; an odd number of crossings flips p_i */
+                    if (xj[i] >= lo[i] && xj[i] <= hi[i]) continue;
+                    const double w = hi[i] - lo[i];
+                    double u = fmod(xj[i] - lo[i], 2.0 * w);
+                    if (u < 0.0) u += 2.0 * w;
+                    if (u > w) { xj[i] = lo[i] + (2.0 * w - u); pj[i] = -pj[i]; }
+                    else xj[i] = lo[i] + u;
+                }
             /* one fused evaluation of log L and its gradient */
             double logl = orc_loglik_impl(lk, logdetP, xj, g);
             int inbox = 1;
@@ -427,7 +461,9 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
              *   noise_mode 1: p <- sqrt(1 - delta_p^2) p + delta_p eps
              *                 (noise added, Section 3, in the form that keeps p ~ N(0, I)) */
             orc_normals(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, d, eps);
-            if (cfg->noise_mode == 1) {
+            if (cfg->noise_inside && out) {
+                /* an outside step only reflects */
+            } else if (cfg->noise_mode == 1) {
                 double keep = sqrt(1.0 - cfg->delta_p * cfg->delta_p);
                 for (int i = 0; i < d; ++i) pj[i] = keep * pj[i] + cfg->delta_p * eps[i];
             } else {
@@ -451,7 +487,7 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
             if (mr >= cfg->min_ref) { saving = 1; t_save = t; }
         }
         for (int j = 0; j < n; ++j) {
-            if (saving && !outside[j]) {
+            if (saving && (!outside[j] || cfg->pick_all)) {
                 ++count[j];
                 /* acceptance word: the low bits of the four words of noise block 0
                  * of this step, which the uniforms (top 23 bits) leave unused */
@@ -461,8 +497,13 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
                 /* keep_last: the App. G ablation that integrates a fixed number of steps and
                  * keeps the last sample, in place of the size-1 reservoir */
                 if (cfg->keep_last || (((uint64_t)word * (uint64_t)count[j]) >> 32) == 0) {
-                    memcpy(xr + (size_t)j * d, x + (size_t)j * d, sizeof(double) * d);
-                    lr[j] = logl_now[j];
+                    if (outside[j]) { /* rejection: the walker keeps its start point */
+                        memcpy(xr + (size_t)j * d, x0 + (size_t)j * d, sizeof(double) * d);
+                        lr[j] = logl0[j];
+                    } else {
+                        memcpy(xr + (size_t)j * d, x + (size_t)j * d, sizeof(double) * d);
+                        lr[j] = logl_now[j];
+                    }
                 }
             }
             if (cfg->prune_after > 0 && consec[j] >= cfg->prune_after) {
@@ -815,12 +856,51 @@ void orc_stats_program(int cap, int n0, int n_ops, const int *op, const int *arg
 }
 
 /* ------------------------------------------------------------------------- */
+/* Cluster regions of the new points                                          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The cluster statistics of Appendix H hold when the live points of cluster p are
+ * spread over p's own region only.  A walker spawned in cluster p (Algorithm 3:
+ * the cluster is chosen with probability Xbar_p / sum Xbar, the start point among
+ * p's survivors) can cross into the region of another cluster while the two are
+ * still connected; kept with label p, it would add points to a region whose volume
+ * another cluster accounts for.  So the new point j is kept only if its nearest
+ * surviving point (FP32 squared distances accumulated in coordinate order, one
+ * fmaf per coordinate, ties to the lower index; the precision the cluster finding
+ * decides in) carries the label it was spawned with; otherwise it is rejected and
+ * the walker returns its start point.
+ * surv[m_s][d] FP32, surv_label[m_s]; xn[k][d] FP32, want[k]: the spawned labels.
+ * keep[j] = 1 when the new point stays.  Returns the number rejected.
+ */
+int orc_territory(int m_s, int d, const float *surv, const int *surv_label, int k, const float *xn,
+                  const int *want, int *keep)
+{
+    int n_rej = 0;
+    for (int j = 0; j < k; ++j) {
+        float best = INFINITY;
+        int bi = -1;
+        for (int i = 0; i < m_s; ++i) {
+            float s = 0.0f;
+            for (int t = 0; t < d; ++t) {
+                float diff = xn[(size_t)j * d + t] - surv[(size_t)i * d + t];
+                s = fmaf(diff, diff, s);
+            }
+            if (s < best) { best = s; bi = i; }
+        }
+        keep[j] = (bi < 0) || (surv_label[bi] == want[j]);
+        n_rej += !keep[j];
+    }
+    return n_rej;
+}
+
+/* ------------------------------------------------------------------------- */
 /* The GGNS driver (Algorithm 3)                                              */
 /* ------------------------------------------------------------------------- */
 
 typedef struct {
     double logz, logz_err, logz_skilling_err, info_h;
-    long n_iter, n_dead, n_like, n_steps_total, n_fallback;
+    long n_iter, n_dead, n_like, n_steps_total, n_fallback, n_region_rejected;
     double dt;
     int n_clusters_final, max_clusters, terminated, status;
 } orc_result_t;
@@ -859,7 +939,7 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
     int *comp = (int *)malloc(sizeof(int) * n_live);
     double *xf_start = (double *)malloc(sizeof(double) * (size_t)n_live * d);
     double *lf_start = (double *)malloc(sizeof(double) * n_live);
-    long n_dead = 0, n_like = 0, n_steps_total = 0, n_fallback = 0;
+    long n_dead = 0, n_like = 0, n_steps_total = 0, n_fallback = 0, n_rejected = 0;
     int status = ORC_OK;
 
     /* Initialise n_live points from the prior and evaluate their likelihoods. */
@@ -987,6 +1067,29 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
             n_like += (long)k * bs.t_stop; n_steps_total += (long)k * bs.t_stop;
             n_fallback += bs.n_fallback;
         }
+        /* --- a new point in another cluster's region returns its start point --- */
+        if (cfg->clustering && cfg->territory) {
+            int nc = 0;
+            for (int c = 0; c < st.cap; ++c) nc += st.alive[c];
+            if (nc > 1) {
+                int ms = 0;
+                for (int i = 0; i < n_live; ++i) {
+                    if (is_dead[i]) continue;
+                    for (int t = 0; t < d; ++t) xf[(size_t)ms * d + t] = (float)x[(size_t)i * d + t];
+                    members[ms++] = label[i];
+                }
+                float *xnf = (float *)malloc(sizeof(float) * (size_t)k * d);
+                int *keep = (int *)malloc(sizeof(int) * k);
+                for (size_t q = 0; q < (size_t)k * d; ++q) xnf[q] = (float)xnew[q];
+                n_rejected += orc_territory(ms, d, xf, members, k, xnf, new_label, keep);
+                for (int j = 0; j < k; ++j)
+                    if (!keep[j]) {
+                        memcpy(xnew + (size_t)j * d, x + (size_t)start_slot[j] * d, sizeof(double) * d);
+                        lnew[j] = logl[start_slot[j]];
+                    }
+                free(xnf); free(keep);
+            }
+        }
         /* --- step-size adaptation from out_frac --- */
         double out_frac = (sum_in + sum_out) > 0 ? (double)sum_out / (double)(sum_in + sum_out) : 0.0;
         if (out_frac > cfg->out_hi) dt *= 0.9;
@@ -1054,6 +1157,7 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
     res->n_like = n_like;
     res->n_steps_total = n_steps_total;
     res->n_fallback = n_fallback;
+    res->n_region_rejected = n_rejected;
     res->dt = dt;
     res->max_clusters = max_clusters;
     int nc = 0;
