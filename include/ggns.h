@@ -101,12 +101,37 @@ typedef struct {
     uint32_t run_id;   /* first run id; run r of a batch uses run_id + r                          */
     long max_iters;    /* iteration cap                                                           */
     long dead_cap;     /* dead-point arena capacity per run; 0 = estimate from d and tol          */
+    /* Readings of Algorithm 5 and of the cluster bookkeeping of Algorithm 3 (Section 2.3,
+     * Section 3).  1 in each selects the form the library defaults to; 0 the printed form. */
+    int noise_inside;  /* 1: the momentum noise perturbs inside steps only, an outside step only
+                          reflects (Section 2.3: a particle can get stuck behind the boundary)
+                          0: every step takes the noise, as Algorithm 5 prints it                */
+    int pick_all;      /* 1: each walker returns a state drawn uniformly over every step of the
+                          saving window; a drawn outside step is rejected and the walker returns
+                          its start point (slice-sampling rejection, Section 2.3)
+                          0: drawn uniformly over the saved inside states only (Algorithm 5)     */
+    int territory;     /* 1: with several clusters alive, a new point whose nearest surviving
+                          point belongs to another cluster returns its start point               */
+    int keep_last;     /* Appendix G ablation: 1 returns the last inside state of the window     */
+    int box_fold;      /* 1: the prior box reflects a walker exactly (its position folds back across
+                          the face, that momentum component flips; no outside step), so only the
+                          iso-likelihood boundary of Algorithm 5 counts as outside
+                          0: leaving the box is an outside step reflected off the violated faces */
+    /* Launch choices; 0 selects the library's own choice.  Options marked (context) are read
+     * from the first configuration of a batch; tile from the first run of each (kind, d).    */
+    int tile;          /* walker tile id + 1: 1..N_TILES (G lanes x E components, ns_tile_shape) */
+    int hss_mode;      /* (context) 1: single pass where resident; 2: three phases always        */
+    int rec_len;       /* (context) step records per walker of the single pass (0: n_steps)     */
+    int noise_ahead;   /* (context) steps of momentum noise drawn ahead (0: 128; -1: none)       */
+    int coop;          /* (context) dense walk sharing P tiles per CTA: 0 auto, -1 off          */
+    int runs_per_group;/* (context) runs per concurrent group and graph (0: all in one group)    */
 } ns_config;
 
 /* Fills the defaults: n_live 200, n_steps 1000, min_steps 0, dt_init 0.1,
- * delta_p 0.2, tol 0.01, min_ref 1, max_ref 3, prune_after 10, termination 0,
+ * delta_p 0.5, tol 0.01, min_ref 1, max_ref 3, prune_after 10, termination 0,
  * clustering 1, noise_mode 1, out_lo 0.05, out_hi 0.15, seed 0, run_id 0,
- * max_iters 100000, dead_cap 0. */
+ * max_iters 100000, dead_cap 0, noise_inside 1, pick_all 1, territory 1,
+ * keep_last 0, box_fold 1 and every launch choice 0 (the library's own). */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context for one run.  Copies the box, the likelihood parameters and
@@ -267,6 +292,18 @@ ns_status ns_knn_components(const float *x_dev, int m, int d, int *comp_dev, int
  * by the caller.  Synchronises `stream`. */
 ns_status ns_knn_components_noalloc(const float *x_dev, int m, int d, int *comp_dev, int *n_comp_host,
                                     void *stream);
+
+/* The region rule of the cluster bookkeeping (Algorithm 3 spawns a new point in
+ * cluster p from one of p's survivors; Appendix H's statistics hold when a
+ * cluster's live points stay in its region): keep_dev[j] = 1 when the nearest of
+ * the m_s survivor rows surv_dev[m_s][d] to the new point xn_dev[j] carries the
+ * label want_dev[j], else 0 (the sampler then returns the walker's start point).
+ * FP32 squared distances accumulated over the coordinates in order by fused
+ * multiply-add; ties go to the lower survivor row; m_s = 0 keeps every point.
+ * All arrays are caller-owned device memory; m_s, k <= 16384, d <= 512;
+ * NS_ERR_ARG otherwise.  Synchronises `stream`. */
+ns_status ns_territory(const float *surv_dev, const int *surv_label_dev, int m_s, const float *xn_dev,
+                       const int *want_dev, int k, int d, int *keep_dev, void *stream);
 
 /* Order of n log-likelihoods (ascending, NaN first, ties by index):
  * order_dev[n].  n <= 16384. */

@@ -75,7 +75,7 @@ struct RunClass {
 // group, because concurrent groups share the SMs and the walkers of one group's
 // single-pass HSS then stop being co-resident.
 struct Group {
-    int r0 = 0, nr = 0, max_n = 0;
+    int r0 = 0, nr = 0, max_n = 0, max_k = 0, max_dpad = 0;
     std::vector<RunClass> classes;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -122,6 +122,7 @@ struct ns_ctx {
     cudaEvent_t start_ev = nullptr;
     double hss_ms_sum = 0.0;
     bool any_clustering = false;
+    bool any_territory = false;  // some run keeps new points in their cluster's region
     int max_n = 0, max_d = 0;
     size_t sel_smem = 0, knn_smem = 0, cl_smem = 0, sort_smem = 0;
     cudaStream_t stream = nullptr;
@@ -197,18 +198,9 @@ int default_tile(int kind, int d)
     return 8;
 }
 
-int env_tile(int kind, int d)
-{
-    char name[64];
-    snprintf(name, sizeof name, "GGNS_TILE_%d_%d", kind, d);
-    const char *v = getenv(name);
-    if (!v) v = getenv("GGNS_TILE");
-    if (!v) return -1;
-    const int t = atoi(v);
-    if (t < 0 || t >= N_TILES) return -1;
-    const Tile T = tile_of(t);
-    return (T.g * T.e >= d) ? t : -1;
-}
+// The walker tile a configuration asks for (cfg.tile = id + 1), or -1 for the
+// library's table; a tile too narrow for d is refused by validate().
+int cfg_tile(const ns_config &c) { return (c.tile >= 1 && c.tile <= N_TILES) ? c.tile - 1 : -1; }
 
 // log det of an SPD matrix (unpivoted Cholesky); NAN if not positive definite.
 double host_logdet(int d, const double *a)
@@ -244,6 +236,13 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
     if (cfg.noise_mode == 1 && !(cfg.delta_p >= 0.0 && cfg.delta_p <= 1.0))
         return fail(nullptr, NS_ERR_ARG, "noise_mode 1 needs 0 <= delta_p <= 1");
     if (cfg.max_iters < 1) return fail(nullptr, NS_ERR_ARG, "max_iters must be >= 1");
+    if (cfg.tile < 0 || cfg.tile > N_TILES) return fail(nullptr, NS_ERR_ARG, "tile must be 0 or a tile id + 1 in [1, %d]", N_TILES);
+    if (cfg.tile > 0) {
+        const Tile T = tile_of(cfg.tile - 1);
+        if (T.g * T.e < b.d) return fail(nullptr, NS_ERR_ARG, "tile %d covers %d < d = %d components", cfg.tile, T.g * T.e, b.d);
+    }
+    if (cfg.hss_mode < 0 || cfg.hss_mode > 2 || cfg.rec_len < 0 || cfg.noise_ahead < -1 || cfg.runs_per_group < 0)
+        return fail(nullptr, NS_ERR_ARG, "launch choices out of range");
     const int K = lk.n_comp;
     switch (lk.kind) {
     case NS_LIK_ISO_GAUSS:
@@ -469,6 +468,11 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
                                         cl.single ? (phase | 4) : phase, cl.smem, cl.prec_in_smem, s));
             ++n;
         }
+    // a new point that landed in another cluster's region returns its start point
+    if (ctx->any_territory) {
+        CU(launch_territory(C, g.r0, g.nr, g.max_k, g.max_dpad, s));
+        ++n;
+    }
     // fork: the tail (step size, counters, iteration count), then the next iteration's noise
     CU(cudaEventRecord(g.pick_ev, s));
     CU(cudaStreamWaitEvent(g.nz_stream, g.pick_ev, 0));
@@ -568,7 +572,7 @@ void ns_config_default(ns_config *c)
     c->n_steps = 1000;
     c->min_steps = 0;
     c->dt_init = 0.1;
-    c->delta_p = 0.2;
+    c->delta_p = 0.5;
     c->tol = 0.01;
     c->min_ref = 1;
     c->max_ref = 3;
@@ -582,6 +586,10 @@ void ns_config_default(ns_config *c)
     c->run_id = 0;
     c->max_iters = 100000;
     c->dead_cap = 0;
+    c->noise_inside = 1;
+    c->pick_all = 1;
+    c->territory = 1;
+    c->box_fold = 1;
 }
 
 const char *ns_last_error(const ns_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -610,7 +618,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.d = box[r].d;
         D.kind = lik[r].kind;
         D.n_comp = kind_has_means(lik[r].kind) ? lik[r].n_comp : 1;
-        int t = env_tile(D.kind, D.d);
+        const int t = cfg_tile(c);
         D.tile = (t >= 0) ? t : default_tile(D.kind, D.d);
         const Tile T = tile_of(D.tile);
         D.d_pad = T.g * T.e;
@@ -624,6 +632,11 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.termination = c.termination;
         D.clustering = c.clustering;
         D.noise_mode = c.noise_mode;
+        D.noise_inside = c.noise_inside ? 1 : 0;
+        D.pick_all = c.pick_all ? 1 : 0;
+        D.territory = c.territory ? 1 : 0;
+        D.keep_last = c.keep_last ? 1 : 0;
+        D.box_fold = c.box_fold ? 1 : 0;
         D.delta_p = (float)c.delta_p;
         D.keep = (float)std::sqrt(std::max(0.0, 1.0 - c.delta_p * c.delta_p));
         D.rosen_scale = (float)lik[r].rosen_scale;
@@ -659,6 +672,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.w_off = w;
         w += D.k;
         ctx->any_clustering |= (D.clustering != 0);
+        ctx->any_territory |= (D.clustering != 0 && D.territory != 0);
         ctx->max_n = std::max(ctx->max_n, D.n_live);
         ctx->max_d = std::max(ctx->max_d, D.d);
     }
@@ -769,9 +783,9 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
     };
     CK(smq());
     {
-        if (const char *v = getenv("GGNS_HSS")) ctx->hss_mode = atoi(v);
+        ctx->hss_mode = (cfg[0].hss_mode == 2) ? 3 : cfg[0].hss_mode;  // ns_config: 2 = three phases always
         long rec_len = 1l << 30;
-        if (const char *v = getenv("GGNS_REC_LEN")) rec_len = std::max(1, atoi(v));
+        if (cfg[0].rec_len > 0) rec_len = cfg[0].rec_len;
         int max_steps = 0, xs = 0;
         long walkers = 0;
         for (int r = 0; r < n_runs; ++r) {
@@ -799,9 +813,10 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 CU(cudaMemcpy(ctx->rec_base_dev, base.data(), sizeof(long) * n_runs, cudaMemcpyHostToDevice));
                 ctx->rec.rec_len = (int)rec_len;
                 ctx->rec.xs = xs;
-                // noise drawn ahead: GGNS_NOISE_STEPS steps per walker (default 128, 0: off)
+                // noise drawn ahead: noise_ahead steps per walker (0: the default 128; -1: off)
                 long nT = 128;
-                if (const char *v = getenv("GGNS_NOISE_STEPS")) nT = std::max(0, atoi(v));
+                if (cfg[0].noise_ahead > 0) nT = cfg[0].noise_ahead;
+                else if (cfg[0].noise_ahead < 0) nT = 0;
                 nT = std::min<long>(nT, rec_len);
                 if (xs % 4 != 0 || walkers * nT * ((long)xs * 4 + 4) > budget) nT = 0;
                 if (nT > 0) {
@@ -814,10 +829,10 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
             CK(mkrec());
         }
     }
-    // run groups: one stream and one graph each (GGNS_RUNS_PER_GROUP runs; default: all runs in one group)
+    // run groups: one stream and one graph each (runs_per_group runs; default: all runs in one group)
     {
         int per = n_runs;
-        if (const char *v = getenv("GGNS_RUNS_PER_GROUP")) per = std::max(1, atoi(v));
+        if (cfg[0].runs_per_group > 0) per = cfg[0].runs_per_group;
         per = std::max(per, (n_runs + 127) / 128);
         auto mkgroups = [&]() -> ns_status {
             CU(cudaEventCreateWithFlags(&ctx->start_ev, cudaEventDefault));
@@ -829,6 +844,8 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                 for (int r = g.r0; r < g.r0 + g.nr; ++r) {
                     const RunDesc &D = ctx->desc[r];
                     g.max_n = std::max(g.max_n, D.n_live);
+                    g.max_k = std::max(g.max_k, D.k);
+                    g.max_dpad = std::max(g.max_dpad, D.d_pad);
                     auto key = std::make_pair(D.kind, D.tile);
                     if (!gcls.count(key)) {
                         gcls[key] = (int)g.classes.size();
@@ -856,9 +873,8 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                         rc.fallback = 0;
                         for (int r : rc.runs) rc.fallback |= (ctx->rec.rec_len < cfg[r].n_steps);
                         // dense likelihoods whose P stays in global memory: walkers of a CTA share each
-                        // tile of P (GGNS_COOP=0 keeps one read of P per walker-step)
-                        const char *cv = getenv("GGNS_COOP");
-                        const bool want = !(cv && atoi(cv) == 0);
+                        // tile of P (coop = -1 keeps one read of P per walker-step)
+                        const bool want = cfg[0].coop >= 0;
                         const bool dense = rc.kind == NS_LIK_DENSE_GAUSS || rc.kind == NS_LIK_DENSE_MIX;
                         if (want && dense && !rc.prec_in_smem && !rc.fallback &&
                             (rc.tile == 6 || rc.tile == 7 || rc.tile == 8)) {
@@ -1611,6 +1627,19 @@ ns_status ns_knn_components(const float *x_dev, int m, int d, int *comp_dev, int
     CU(cudaMemcpyAsync(&h, nc.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (n_comp_host) *n_comp_host = h;
+    return NS_OK;
+}
+
+ns_status ns_territory(const float *surv_dev, const int *surv_label_dev, int m_s, const float *xn_dev,
+                       const int *want_dev, int k, int d, int *keep_dev, void *stream)
+{
+    ns_ctx *ctx = nullptr;
+    if (m_s < 0 || m_s > NLIVE_MAX || k < 0 || k > NLIVE_MAX || d < 1 || d > DMAX || (m_s > 0 && (!surv_dev || !surv_label_dev)) ||
+        (k > 0 && (!xn_dev || !want_dev || !keep_dev)))
+        return NS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CU(launch_territory_plain(surv_dev, surv_label_dev, m_s, xn_dev, want_dev, k, d, keep_dev, s));
+    CU(cudaStreamSynchronize(s));
     return NS_OK;
 }
 

@@ -55,6 +55,8 @@ __host__ __device__ inline int noise_steps(int nT, int t_stop_last)
 struct RunDesc {
     int d, d_pad, n_live, k, kind, n_comp;
     int n_steps, min_steps, min_ref, max_ref, prune_after, termination, clustering, noise_mode;
+    int noise_inside, pick_all, territory, keep_last;  // readings of Algorithm 5 (ns_config)
+    int box_fold, pad2_;                               // exact reflection off the prior box
     float delta_p, keep, rosen_scale, lik_const;
     float torus_a, torus_b, torus_c;  // TORUS: sine and cosine frequencies, offset
     double log_tol, out_lo, out_hi, dt_init;

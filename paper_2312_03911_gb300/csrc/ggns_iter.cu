@@ -889,22 +889,31 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
     }
     if (w >= W) return;
     const long base = rec_base[r] + (long)w * R.rec_len;
+    // the steps of the window that enter the reservoir: inside steps from t_save on;
+    // with pick_all every step, a drawn outside step rejecting (the start point)
     int pick = 0, count = 0, nout = 0;
+    bool pick_out = false;
     for (int t0 = 1; t0 <= tstop; t0 += 32) {
         const int t = t0 + lane;
         uint2 m = make_uint2(0u, 0u);
         if (t <= tstop) m = R.meta[base + t - 1];
         const bool in_win = t <= tstop;
         const bool outside = in_win && m.y != 0u;
-        const bool saved = in_win && !outside && t >= ts0;
+        const bool saved = in_win && (!outside || D.pick_all) && t >= ts0;
         const unsigned smask = __ballot_sync(0xffffffffu, saved);
         const int cnt = count + __popc(smask & ((1u << lane) - 1u)) + 1;
-        const bool acc = saved && ((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(cnt)) >> 32) == 0;
+        const bool acc = saved && (D.keep_last || ((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(cnt)) >> 32) == 0);
         const unsigned amask = __ballot_sync(0xffffffffu, acc);
-        if (amask) pick = t0 + 31 - __clz(amask);
+        const unsigned omask = __ballot_sync(0xffffffffu, outside);
+        if (amask) {
+            const int hl = 31 - __clz(amask);
+            pick = t0 + hl;
+            pick_out = (omask >> hl) & 1u;
+        }
         count += __popc(smask);
-        nout += __popc(__ballot_sync(0xffffffffu, outside));
+        nout += __popc(omask);
     }
+    if (pick_out) pick = 0;  // rejected: the walker keeps its start point
     const int slot = C.order[D.pt_off + w];
     float *dst = C.fa + D.x_off + (long)slot * dp;
     const float *src = (pick > 0) ? R.x + (base + pick - 1) * R.xs
@@ -917,6 +926,101 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
         if (pick <= 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
     }
+}
+
+// ------------------------------------------------------------------------
+// Cluster regions of the new points (the bookkeeping of Appendix H holds when
+// the live points of a cluster lie in that cluster's region only)
+// ------------------------------------------------------------------------
+// The nearest of m candidate rows (FP32 squared distance accumulated over the d
+// coordinates in order by fused multiply-add; ties to the lower candidate key)
+// to the point q held in shared memory.  One warp; lane l scans candidates l,
+// l + 32, ...; returns the winning candidate position in every lane.
+// cand(i) gives the row of candidate i and key(i) its tie-break key.
+template <typename RowF, typename KeyF>
+__device__ __forceinline__ int warp_nearest(const float *q, int d, int m, RowF cand, KeyF key)
+{
+    const int lane = threadIdx.x & 31;
+    float best = INFINITY;
+    int bi = -1, bk = 0x7fffffff;
+    for (int i = lane; i < m; i += 32) {
+        const float *row = cand(i);
+        float s = 0.f;
+        for (int c = 0; c < d; ++c) {
+            const float diff = q[c] - row[c];
+            s = __fmaf_rn(diff, diff, s);
+        }
+        const int k = key(i);
+        if (s < best || (s == best && k < bk)) {
+            best = s;
+            bi = i;
+            bk = k;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ob < best || (ob == best && ok < bk)) {
+            best = ob;
+            bi = oi;
+            bk = ok;
+        }
+    }
+    return bi;
+}
+
+constexpr int TER_WARPS = 4;
+
+// Walker w's new point (slot order[w]) stays only if its nearest surviving point
+// (slots order[k .. n_live), ties to the lower slot) carries the label it was
+// spawned with; otherwise the slot takes the walker's start point and its log L.
+// Runs with clustering and the territory rule on; skipped when every survivor has
+// the new point's label (one cluster alive).
+__global__ void __launch_bounds__(TER_WARPS * 32) k_territory(DevCtx C, int r0)
+{
+    extern __shared__ float tsm[];
+    const int r = r0 + blockIdx.y;
+    const RunDesc &D = C.desc[r];
+    const RunState *S = C.state + r;
+    if (S->done || !D.clustering || !D.territory) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * TER_WARPS + warp;
+    if (w >= D.k) return;
+    const int n = D.n_live, k = D.k, dp = D.d_pad, d = D.d;
+    const int *ord = C.order + D.pt_off;
+    const int want = C.new_label[D.w_off + w];
+    bool other = false;
+    for (int i = k + lane; i < n; i += 32) other |= (C.label[D.pt_off + ord[i]] != want);
+    if (!__any_sync(0xffffffffu, other)) return;
+    const int slot = ord[w];
+    float *q = tsm + (long)warp * dp;
+    const float *xs = C.fa + D.x_off;
+    for (int c = lane; c < dp; c += 32) q[c] = xs[(long)slot * dp + c];
+    __syncwarp();
+    const int bi = warp_nearest(q, d, n - k, [&](int i) { return xs + (long)ord[k + i] * dp; },
+                                [&](int i) { return ord[k + i]; });
+    if (bi < 0 || C.label[D.pt_off + ord[k + bi]] == want) return;
+    const int s0 = C.start_slot[D.w_off + w];
+    for (int c = lane; c < dp; c += 32) C.fa[D.x_off + (long)slot * dp + c] = xs[(long)s0 * dp + c];
+    if (lane == 0) C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
+}
+
+// Component form for the tests: keep[j] = 1 if the nearest of the m_s survivor
+// rows surv[m_s][d] (ties to the lower row) to xn[j] carries label want[j].
+__global__ void k_territory_plain(const float *surv, const int *surv_label, int m_s, const float *xn,
+                                  const int *want, int k, int d, int *keep)
+{
+    extern __shared__ float tsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * TER_WARPS + warp;
+    if (j >= k) return;
+    float *q = tsm + (long)warp * d;
+    for (int c = lane; c < d; c += 32) q[c] = xn[(long)j * d + c];
+    __syncwarp();
+    const int bi = warp_nearest(q, d, m_s, [&](int i) { return surv + (long)i * d; }, [&](int i) { return i; });
+    if (lane == 0) keep[j] = (bi < 0 || surv_label[bi] == want[j]) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------------
@@ -1775,6 +1879,20 @@ cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k,
                             cudaStream_t s)
 {
     k_hss_pick<<<dim3((max_k + PICK_WARPS - 1) / PICK_WARPS, nr), PICK_WARPS * 32, 0, s>>>(C, runs, R, rec_base);
+    return cudaGetLastError();
+}
+cudaError_t launch_territory(const DevCtx &C, int r0, int n_runs, int max_k, int max_dpad, cudaStream_t s)
+{
+    k_territory<<<dim3((max_k + TER_WARPS - 1) / TER_WARPS, n_runs), TER_WARPS * 32,
+                  sizeof(float) * TER_WARPS * max_dpad, s>>>(C, r0);
+    return cudaGetLastError();
+}
+cudaError_t launch_territory_plain(const float *surv, const int *surv_label, int m_s, const float *xn, const int *want,
+                                   int k, int d, int *keep, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    k_territory_plain<<<(k + TER_WARPS - 1) / TER_WARPS, TER_WARPS * 32, sizeof(float) * TER_WARPS * d, s>>>(
+        surv, surv_label, m_s, xn, want, k, d, keep);
     return cudaGetLastError();
 }
 cudaError_t launch_term_cluster_sort(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,

@@ -35,6 +35,35 @@ __device__ __forceinline__ void wrap_periodic(const RunDesc &D, const ParView &P
     }
 }
 
+// Prior box with box_fold: a component that left [lo, hi] is reflected back exactly
+// (the path unfolded on a line of period 2w folds into the box; an odd number of
+// crossings flips that momentum component), so the walker never leaves the prior
+// and the box takes no outside step.  Padded components (lo = hi = x = 0) never fold.
+template <int KIND, int E>
+__device__ __forceinline__ void fold_box(const RunDesc &D, const ParView &P, float (&x)[E], float (&p)[E], int c0)
+{
+    if constexpr (KIND != NS_LIK_TORUS) {
+        if (!D.box_fold) return;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int c = c0 + e;
+            const float lo = P.lo[c], hi = P.hi[c];
+            if (!(x[e] < lo || x[e] > hi)) continue;
+            const float w = hi - lo, w2 = 2.f * w;
+            float u = x[e] - lo;
+            u -= w2 * floorf(u / w2);
+            if (u >= w2) u -= w2;  // rounding of the quotient
+            if (u < 0.f) u = 0.f;
+            if (u > w) {
+                x[e] = lo + (w2 - u);
+                p[e] = -p[e];
+            } else {
+                x[e] = lo + u;
+            }
+        }
+    }
+}
+
 // Copy the parameter block of run D into shared memory (the precision matrix
 // only when `prec_in_smem`); returns the view.  Call by the whole CTA.
 __device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *sm, bool prec_in_smem)
@@ -576,6 +605,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 #pragma unroll
     for (int e = 0; e < E; ++e) vmask[e] = (c0 + e < D.d) ? 1.f : 0.f;  // padded components keep p = 0
     int w = 0, t = 0, nref = 0, consec = 0, count = 0, nin = 0, nout = 0;
+    int res_start = 0;  // the reservoir holds a rejected (outside) step: emit the start point
     float res_ll = 0.f;
     bool active = false, exhausted = false;
 
@@ -601,7 +631,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         if (c0 + e >= D.d) p[e] = 0.f;
                         xr[e] = x[e];
                     }
-                    t = nref = consec = count = nin = nout = 0;
+                    t = nref = consec = count = nin = nout = res_start = 0;
                     res_ll = 0.f;
                     // archive the dead point that this walker's output will replace
                     const int ks = C.order[D.pt_off + w];
@@ -619,6 +649,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                     }
                     const int *wi = C.wint + (D.w_off + w) * 8;
                     t = wi[0]; nref = wi[1]; consec = wi[2]; count = wi[3]; nin = wi[4]; nout = wi[5];
+                    res_start = wi[7];
                     res_ll = C.wres_logl[D.w_off + w];
                 }
             }
@@ -641,16 +672,18 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                     if (lig == 0) {
                         int *wi = C.wint + (D.w_off + w) * 8;
                         wi[0] = t; wi[1] = nref; wi[2] = consec; wi[3] = count; wi[4] = nin; wi[5] = nout;
+                        wi[7] = res_start;
                         C.wres_logl[D.w_off + w] = res_ll;
                         if (phase == 0) atomicMax(&S->t_save, (nref >= D.min_ref) ? t : D.n_steps + 1);
                         else atomicMax(&S->t_stop, t);
                     }
                 } else {
-                    // emit: a uniform pick among the saved inside states, else the start point
+                    // emit: the reservoir pick, else (nothing saved, or a rejected outside
+                    // step drawn) the start point
                     const int slot = C.order[D.pt_off + w];
                     float *dst = C.fa + D.x_off + (long)slot * dp + c0;
                     float out_ll;
-                    if (count > 0) {
+                    if (count > 0 && !res_start) {
 #pragma unroll
                         for (int e = 0; e < E; ++e) dst[e] = xr[e];
                         out_ll = res_ll;
@@ -666,7 +699,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
                         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(nin));
                         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
-                        if (count == 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
+                        if (count == 0 || res_start) C.wint[(D.w_off + w) * 8 + 6] = 1;
                     }
                 }
                 active = false;
@@ -686,6 +719,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
+        fold_box<KIND, E>(D, P, x, p, c0);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
         int outbox = 0;
         float nb[E];
@@ -726,8 +760,8 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                 for (int e = 0; e < E; ++e) p[e] = -p[e];
             }
         }
-        // momentum noise
-        if (stepping) {
+        // momentum noise (with noise_inside, an outside step only reflects)
+        if (stepping && !(outside && D.noise_inside)) {
             if (D.noise_mode == 1) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * vmask[e]);
@@ -735,14 +769,18 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 #pragma unroll
                 for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
             }
+        }
+        if (stepping) {
             nref += outside ? 1 : 0;
             if (outside) { ++nout; ++consec; } else { ++nin; consec = 0; }
         }
-        // trajectory preservation: size-1 reservoir over the saved inside states
-        const bool save = stepping && !outside && (ts >= t_save);
+        // trajectory preservation: size-1 reservoir over the steps of the saving window
+        // (inside steps only; with pick_all every step, a drawn outside step rejecting)
+        const bool save = stepping && (!outside || D.pick_all) && (ts >= t_save);
         if (save) {
             ++count;
-            if (((static_cast<uint64_t>(res_word) * static_cast<uint64_t>(count)) >> 32) == 0) {
+            if (D.keep_last || ((static_cast<uint64_t>(res_word) * static_cast<uint64_t>(count)) >> 32) == 0) {
+                res_start = outside ? 1 : 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) xr[e] = x[e];
                 res_ll = ll;
@@ -950,6 +988,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
+        fold_box<KIND, E>(D, P, x, p, c0);
         float ll;
         if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
@@ -993,12 +1032,15 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             }
         }
         if (stepping) {
-            if (D.noise_mode == 1) {
+            // momentum noise (with noise_inside, an outside step only reflects)
+            if (!(outside && D.noise_inside)) {
+                if (D.noise_mode == 1) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * ecur[e] * vmask[e]);
-            } else {
+                    for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * ecur[e] * vmask[e]);
+                } else {
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, ecur[e], 1.f);
+                    for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, ecur[e], 1.f);
+                }
             }
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;

@@ -43,7 +43,11 @@ class Config(C.Structure):
                 ("delta_p", C.c_double), ("tol", C.c_double), ("min_ref", C.c_int), ("max_ref", C.c_int),
                 ("prune_after", C.c_int), ("termination", C.c_int), ("clustering", C.c_int),
                 ("noise_mode", C.c_int), ("out_lo", C.c_double), ("out_hi", C.c_double), ("seed", C.c_uint64),
-                ("run_id", C.c_uint32), ("max_iters", C.c_long), ("dead_cap", C.c_long)]
+                ("run_id", C.c_uint32), ("max_iters", C.c_long), ("dead_cap", C.c_long),
+                ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int), ("keep_last", C.c_int),
+                ("box_fold", C.c_int),
+                ("tile", C.c_int), ("hss_mode", C.c_int), ("rec_len", C.c_int), ("noise_ahead", C.c_int),
+                ("coop", C.c_int), ("runs_per_group", C.c_int)]
 
 
 class Result(C.Structure):
@@ -58,7 +62,7 @@ EXPORTS = ["ns_config_default", "ns_create", "ns_batch_create", "ns_set_stream",
            "ns_profile", "ns_result",
            "ns_result_run", "ns_samples", "ns_grad_logz", "ns_state_save", "ns_state_load", "ns_last_error",
            "ns_destroy", "ns_philox", "ns_lik_forward", "ns_lik_backward", "ns_hss", "ns_knn_components",
-           "ns_sort_logl", "ns_stats_update", "ns_knn_components_noalloc", "ns_set_means"]
+           "ns_sort_logl", "ns_stats_update", "ns_knn_components_noalloc", "ns_set_means", "ns_territory"]
 
 _lib = None
 _lock = threading.Lock()
@@ -111,6 +115,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
                              C.POINTER(C.c_long), _vp]
         L.ns_knn_components.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int), _vp]
         L.ns_sort_logl.argtypes = [_vp, C.c_int, _vp, _vp]
+        L.ns_territory.argtypes = [_vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp]
         L.ns_knn_components_noalloc.argtypes = [_vp, C.c_int, C.c_int, _vp, C.POINTER(C.c_int), _vp]
         L.ns_stats_update.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
@@ -301,6 +306,12 @@ def knn_components_noalloc(x_ptr, m, d, comp_ptr, stream=None) -> int:
     nc = C.c_int()
     _check(load().ns_knn_components_noalloc(_vp(x_ptr), int(m), int(d), _vp(comp_ptr), C.byref(nc), _vp(stream)))
     return nc.value
+
+
+def territory(surv_ptr, surv_label_ptr, m_s, xn_ptr, want_ptr, k, d, keep_ptr, stream=None):
+    """ns_territory: keep[j] = 1 when new point j's nearest survivor carries label want[j]."""
+    _check(load().ns_territory(_vp(surv_ptr), _vp(surv_label_ptr), int(m_s), _vp(xn_ptr), _vp(want_ptr), int(k),
+                               int(d), _vp(keep_ptr), _vp(stream)))
 
 
 def sort_logl(logl_ptr, n, order_ptr, stream=None):

@@ -34,7 +34,21 @@ def test_config_defaults_without_gpu():
     c = ggns.default_config()
     assert (c.n_live, c.n_steps, c.min_ref, c.max_ref, c.termination, c.clustering, c.noise_mode) == \
         (200, 1000, 1, 3, 0, 1, 1)
-    assert c.tol == pytest.approx(0.01) and c.dt_init == pytest.approx(0.1) and c.delta_p == pytest.approx(0.2)
+    assert c.tol == pytest.approx(0.01) and c.dt_init == pytest.approx(0.1) and c.delta_p == pytest.approx(0.5)
+    # the readings of Algorithm 5 the library defaults to, and the library's own launch choices
+    assert (c.noise_inside, c.pick_all, c.territory, c.keep_last, c.box_fold) == (1, 1, 1, 0, 1)
+    assert (c.tile, c.hss_mode, c.rec_len, c.noise_ahead, c.coop, c.runs_per_group) == (0, 0, 0, 0, 0, 0)
+
+
+def test_config_struct_matches_the_header():
+    """The binding's ns_config mirrors include/ggns.h field by field (names in order)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "ggns.h")).read()
+    body = src[src.index("typedef struct {\n    int n_live;"):]
+    body = body[:body.index("} ns_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"(\w+)\s*;", body)
+    assert names == [f for f, _ in ggns.Config._fields_]
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu():
@@ -57,4 +71,6 @@ def test_autotune_candidates_hold_d_without_doubling_the_padding():
         for t in c:
             g, e = autotune.TILES[t]
             assert d <= g * e <= 2 * max(d, 2)
-    assert autotune.env_name(1, 32) == "GGNS_TILE_1_32"
+    run = dict(spec=dict(kind=1, d=32), cfg=dict(n_live=100))
+    out = autotune.apply({(1, 32): (4, 0)}, [run])
+    assert out[0]["cfg"]["tile"] == 5 and out[0]["cfg"]["coop"] == 0 and "tile" not in run["cfg"]
