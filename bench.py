@@ -1,17 +1,21 @@
-"""Benchmark: HSS point-steps/s and time-to-log-Z of gradient-guided nested sampling.
+"""Benchmark: HSS point-steps/s of gradient-guided nested sampling, and time-to-log-Z.
 
-One step = one complete pass of the hot path over one batch: R seeded replicas of
-the d=32 four-component mixture workload (n_live=1000, clustering on) run to
-termination in one context -- prior draws, per iteration cluster finding,
-selection, FP64 statistics, spawn, the three HSS phases and the tail, then the
-final sweep, the posterior information and d log Z / d means of every replica.
-The replicas are the R = ceil((3 sigma / 0.2)^2) runs whose mean meets the
-0.2-nat criterion.
+Headline workload c5 (the largest single-GPU configuration): d=512, an equal mixture
+of 8 Gaussians sharing one dense precision matrix, n_live=4000.  One step = one
+complete run in one context: prior draws, every iteration (selection, FP64
+statistics, spawn, the HSS walk, the step-size tail), the final sweep, the
+posterior weights and d log Z / d means.  value = HSS point-steps/s over the step.
+
+Beside it, time-to-log-Z on c2x17: 17 seeded replicas of the d=32 four-component
+mixture (n_live=1000, clustering on) in one batch, the R = ceil((3 sigma / 0.2)^2)
+replicas whose mean meets the 0.2-nat criterion; its time is reported only when
+the replicas' mean is within 0.2 nats of the closed form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ggns|reference]
+                  [--workload c5|c2]
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own R
-replicas (independent runs: no collective on the data path, weak scaling).
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own runs
+(independent runs: no collective on the data path, weak scaling).
 """
 from __future__ import annotations
 
@@ -36,21 +40,19 @@ from paper_2312_03911_gb300 import workloads as W  # noqa: E402
 
 METRIC = "HSS point-steps/s"
 UNIT = "point-steps/s"
-WORKLOAD = "c2"
-DEFAULT_REPLICAS = 17
+C2_REPLICAS = 17
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per k_hss1 launch from one ncu capture of this workload
-# (profiles/k_hss1_c2x17.md), valid only for the kernel sources with these hashes.
-HSS_TRAFFIC_BYTES = 130.85e6
-HSS_TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "29d4e8cec9657d33",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "2215bb2dc5d7ffc3"}
 SMS = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only
+# for the kernel sources with these hashes (None: not captured for these sources).
+TRAFFIC = {"c5": None, "c2": None}
+TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": None,
+                   "paper_2312_03911_gb300/csrc/ggns_internal.cuh": None}
 
 
 def lane_ops_per_point_step(d: int, K: int, out_frac: float, rng: bool = True) -> float:
-    """Algorithmic lane operations of one walker step of the isotropic-mixture HSS
-    (the per-unit figure of the roofline; derivation in the design notes):
+    """Algorithmic lane operations of one walker step of the isotropic-mixture HSS:
     move d FMA; likelihood 2Kd (difference, FMA) + K exp + 1 log + 12 scalar;
     score Kd FMA + d scale; box test 2d; reflection 3d on outside steps; noise
     2d (scale, FMA).  With rng: the step's d normals, d/4 Philox4x32-10 blocks x
@@ -65,6 +67,13 @@ def lane_ops_per_point_step(d: int, K: int, out_frac: float, rng: bool = True) -
     noise = 2 * d
     draw = (d / 4) * 100 + 4 * d + 4 * d if rng else 0.0
     return move + lik + score + box + refl + noise + draw
+
+
+def dense_mix_flops_per_point_step(d: int, K: int) -> float:
+    """Algorithmic FLOPs of one walker step of the dense-mixture likelihood: the contraction
+    y = P x (2 d^2; the mixture shares P, so P mu_k is precomputed) and the K quadratic forms
+    and score terms (x - mu_k).(y - P mu_k), about 4 K d."""
+    return 2.0 * d * d + 4.0 * K * d
 
 
 class ClockSampler:
@@ -119,9 +128,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def replicas(R: int, rank: int):
-    w = W.workload(WORKLOAD)
-    return w, [dict(w, cfg=dict(w["cfg"], run_id=rank * R + r)) for r in range(R)]
+def runs_of(name: str, n: int, rank: int):
+    """n seeded runs of a workload (rank r takes run ids r*n .. r*n+n-1)."""
+    w = W.workload(name)
+    return w, [dict(w, cfg=dict(w["cfg"], run_id=rank * n + r)) for r in range(n)]
 
 
 def max_over_ranks(t: float, dist, device: str) -> float:
@@ -144,14 +154,17 @@ def sum_over_ranks(x: float, dist, device: str) -> float:
     return float(tt.item())
 
 
-def measured_traffic():
-    """The profiled traffic per launch, or None once the kernel sources differ from the profiled ones."""
+def measured_traffic(name: str):
+    """The profiled DRAM traffic per launch of the workload's dominant kernel, or None when it
+    was not captured for the current kernel sources."""
     import hashlib
-    for rel, h in HSS_TRAFFIC_SOURCES.items():
+    if TRAFFIC.get(name) is None:
+        return None
+    for rel, h in TRAFFIC_SOURCES.items():
         with open(os.path.join(ROOT, rel), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
+            if h is None or hashlib.sha256(f.read()).hexdigest()[:16] != h:
                 return None
-    return HSS_TRAFFIC_BYTES
+    return TRAFFIC[name]
 
 
 def load_peaks():
@@ -164,36 +177,50 @@ def load_peaks():
 # --------------------------------------------------------------------------- #
 # Oracle leg (CPU baseline / reference arm)                                     #
 # --------------------------------------------------------------------------- #
-def oracle_sample(n_runs: int, threads: int, seed_base: int = 0):
-    """Run n_runs full oracle runs of the workload on `threads` host threads (the
-    oracle is single-threaded per run; ctypes releases the GIL).  Returns
-    (point-steps, seconds, logZs)."""
+def oracle_sample(name: str, threads: int, seed_base: int = 0):
+    """A bounded sample of the workload on the oracle, on `threads` host threads (the oracle is
+    single-threaded per call; ctypes releases the GIL).  c2: one complete run per thread.  c5 (a
+    complete run takes hours on a core): per thread, one HSS call of Algorithm 5 of 4 walkers
+    started at prior points, 40 steps, on the c5 likelihood.  Returns (point-steps, seconds)."""
+    import numpy as np
     import oracle
-    w = W.workload(WORKLOAD)
+    w = W.workload(name)
     lik = oracle.Likelihood.from_spec(w["spec"])
-    out = [None] * n_runs
-    nxt = [0]
+    ld = lik.logdet()
+    out = [0] * threads
     lock = threading.Lock()
 
-    def worker():
-        while True:
-            with lock:
-                i = nxt[0]
-                nxt[0] += 1
-            if i >= n_runs:
-                return
+    def worker(i):
+        if name == "c5":
+            d = w["spec"]["d"]
+            rng = np.random.default_rng(seed_base + i)
+            x0 = rng.uniform(-1, 1, size=(4, d))
+            l0 = np.array([lik.loglik(v) for v in x0])
+            cfg = oracle.make_cfg(**dict(w["cfg"], run_id=seed_base + i, n_steps=40, min_steps=40,
+                                         max_ref=10**6))
+            o = oracle.hss_batch(lik, w["lo"], w["hi"], cfg, 1, x0, l0, float(l0.min()) - 50.0, 0.002)
+            n = 4 * o["t_stop"]
+        else:
             cfg = oracle.make_cfg(**dict(w["cfg"], run_id=seed_base + i))
-            r = oracle.run(lik, w["lo"], w["hi"], cfg)
-            out[i] = (r["n_steps_total"], r["logz"])
+            n = oracle.run(lik, w["lo"], w["hi"], cfg)["n_steps_total"]
+        with lock:
+            out[i] = n
 
+    del ld
     t0 = time.perf_counter()
-    ths = [threading.Thread(target=worker) for _ in range(threads)]
+    ths = [threading.Thread(target=worker, args=(i,)) for i in range(threads)]
     for t in ths:
         t.start()
     for t in ths:
         t.join()
-    dt = time.perf_counter() - t0
-    return sum(o[0] for o in out), dt, [o[1] for o in out]
+    return sum(out), time.perf_counter() - t0
+
+
+def sample_note(name: str, threads: int, n: int, t: float) -> str:
+    if name == "c5":
+        return (f"{threads} host threads, each one HSS call (Algorithm 5) of 4 walkers x 40 steps on the c5 "
+                f"likelihood from prior points ({n} point-steps in {t:.1f} s)")
+    return f"{threads} complete oracle runs of c2, one per host thread ({n} point-steps in {t:.1f} s)"
 
 
 def reference_arm(args):
@@ -202,37 +229,126 @@ def reference_arm(args):
         return 0
     import oracle
     oracle.build()
-    threads = min(os.cpu_count() or 1, args.replicas)
-    cfg_desc = workload_config(args)
+    threads = os.cpu_count() or 1
+    if args.workload == "c2":
+        threads = min(threads, C2_REPLICAS)
     for i in range(args.warmup):
-        oracle_sample(1, 1, seed_base=10_000 + i)
+        oracle_sample(args.workload, 1, seed_base=10_000 + i)
     times, steps = [], []
     for i in range(args.steps):
-        n, t, _ = oracle_sample(threads, threads, seed_base=20_000 + i * threads)
+        n, t = oracle_sample(args.workload, threads, seed_base=20_000 + i * threads)
         times.append(t)
         steps.append(n)
     value = sum(steps) / sum(times)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg_desc,
-            "impl": "reference",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{threads} complete oracle runs of the workload per step, one per thread"},
+                             "sample": sample_note(args.workload, threads, steps[-1], times[-1])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def workload_config(args):
-    return {"workload": f"{WORKLOAD}x{args.replicas}: {args.replicas} seeded replicas of the d=32 equal mixture of "
-                        f"4 isotropic Gaussians (sigma 0.05), prior U[-1,1]^32, n_live=1000, clustering on, "
-                        f"XL-peak tol 0.01", "replicas": args.replicas, "d": 32, "n_live": 1000, "n_comp": 4,
-            "noise_mode": 1, "delta_p": 0.2, "l2": "flushed between steps (256 MiB write)"}
+def workload_config(name: str):
+    if name == "c5":
+        return {"workload": "c5: d=512 equal mixture of 8 Gaussians sharing one dense precision P = Sigma^-1, "
+                            "Sigma = Q diag(lambda) Q^T (Q from QR of a seeded normal matrix, lambda log-uniform "
+                            "in [1e-3, 1e-1]), means U[-0.5,0.5]^512, prior U[-1,1]^512, n_live=4000, one complete "
+                            "run per step (prior draws to the final sweep, posterior weights, d logZ/d means)",
+                "d": 512, "n_live": 4000, "n_comp": 8, "runs": 1,
+                "l2": "inputs larger than L2 (P and the 4000 x 512 live points are re-read every iteration; "
+                      "256 MiB written between steps)"}
+    return {"workload": f"c2x{C2_REPLICAS}: {C2_REPLICAS} seeded replicas of the d=32 equal mixture of 4 "
+                        "isotropic Gaussians (sigma 0.05), prior U[-1,1]^32, n_live=1000, clustering on, "
+                        "XL-peak tol 0.01", "replicas": C2_REPLICAS, "d": 32, "n_live": 1000, "n_comp": 4,
+            "l2": "flushed between steps (256 MiB write)"}
 
 
 # --------------------------------------------------------------------------- #
 # GPU leg                                                                       #
 # --------------------------------------------------------------------------- #
+def _timed_steps(s, R, steps, stream, flush, dist, seed0, grad=True):
+    """Complete runs of the context's R runs per step (restart with a new seed, run to the final
+    sweep, posterior information and d log Z / d means of every run), timed with CUDA events on
+    the context's stream; max over ranks."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times, pts, logz, errs = [], [], [], []
+    for i in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ev0.record(stream)
+        s.restart(seed0 + i)
+        s.run()
+        res = [s.result(r) for r in range(R)]
+        if grad:
+            for r in range(R):
+                s.grad_logz(r)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, dist, "cuda"))
+        pts.append(sum(r["n_steps_total"] for r in res))
+        logz.append([r["logz"] for r in res])
+        errs.append([r["logz_err"] for r in res])
+    return times, pts, logz, errs
+
+
+def _c2_time_to_logz(ggns, torch, stream, flush, rank, warmup):
+    """c2x17 in one batch: time to a mean log Z of the 17 replicas, against the plain path."""
+    w, runs = runs_of("c2", C2_REPLICAS, rank)
+    s = ggns.Sampler(runs, stream=stream.cuda_stream)
+    for i in range(max(1, warmup)):
+        s.restart(W.SEED_BASE + 3000 + i)
+        s.run()
+    s.profile(reset=True)
+    times, pts, logz, errs = _timed_steps(s, C2_REPLICAS, 2, stream, flush, None, W.SEED_BASE + 4000)
+    prof = s.profile(reset=True)
+    s.close()
+    truth = W.truth_logz(w)
+    z = np.array(logz)
+    ms = 1000.0 * sum(times) / len(times)
+    dz = float(z.mean() - truth)
+    sem = float(z.std(ddof=1) / math.sqrt(z.size))
+    meets = abs(dz) < 0.2
+    # the plain GPU path: the same replicas one after another, one pre-created context each,
+    # one host-synchronised launch chain per iteration (no graph, no batching); CUDA events on
+    # the default stream bracket the whole sequence
+    plains = [ggns.Sampler([r]) for r in runs]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for sp in plains:
+        while not sp.step(1):
+            pass
+        sp.run(0)
+        sp.result(0)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for sp in plains:
+        sp.close()
+    hss_s = prof["hss_ms"] / 1000.0
+    ops = lane_ops_per_point_step(32, 4, 0.12, rng=not prof.get("noise_steps", 0) > 0)
+    return {"workload": workload_config("c2")["workload"], "point_steps_per_s": sum(pts) / sum(times),
+            "ms_per_batch": ms, "logz_mean": float(z.mean()), "logz_truth": truth, "dlogz_mean": dz,
+            "dlogz_sem": sem, "logz_sd": float(z.std(ddof=1)), "logz_err_mean": float(np.mean(errs)),
+            "runs": int(z.size), "meets_0p2": meets,
+            "time_to_logz_ms": ms if meets else None,
+            "time_to_logz_note": None if meets else f"mean log Z of the replicas is {dz:+.2f} nats off the closed form",
+            "plain": {"time_to_logz_ms": plain_ms if meets else None, "ms": plain_ms,
+                      "what": "the 17 replicas one after another, one pre-created context each, one "
+                              "host-synchronised launch chain per iteration (no graph, no batching), CUDA events",
+                      "speedup": plain_ms / ms},
+            "hss_roofline": {"bound": "alu", "achieved": ops * sum(pts) / hss_s / 1e12 if hss_s > 0 else None,
+                             "unit": "Tlane-op/s", "ops_per_point_step": ops,
+                             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times))}}
+
+
 def gpu_arm(args):
     import torch
     from paper_2312_03911_gb300 import build as B
@@ -254,128 +370,106 @@ def gpu_arm(args):
         dist.barrier()
     ggns.load()
     stream = torch.cuda.current_stream()
-    R = args.replicas
-    w, runs = replicas(R, rank)
+    name = args.workload
+    R = 1 if name == "c5" else C2_REPLICAS
+    w, runs = runs_of(name, R, rank)
     s = ggns.Sampler(runs, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    truth = W.truth_logz(w)
-
-    def one_step(seed):
-        s.restart(seed)
+    for i in range(args.warmup):
+        s.restart(W.SEED_BASE + 1000 + i)
         s.run()
-        res = [s.result(r) for r in range(R)]
         for r in range(R):
             s.grad_logz(r)
-        return res
-
-    for i in range(args.warmup):
-        one_step(W.SEED_BASE + 1000 + i)
     s.profile(reset=True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    times, pts, logz, errs = [], [], [], []
     with ClockSampler() as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            if dist is not None:
-                dist.barrier()
-            ev0.record(stream)
-            res = one_step(W.SEED_BASE + 2000 + i)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            t = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, dist, "cuda")
-            times.append(t)
-            pts.append(sum(r["n_steps_total"] for r in res))
-            logz.append([r["logz"] for r in res])
-            errs.append([r["logz_err"] for r in res])
+        times, pts, logz, errs = _timed_steps(s, R, args.steps, stream, flush, dist, W.SEED_BASE + 2000)
     prof = s.profile(reset=True)
     clocks = clk.summary()
     tot_pts = sum_over_ranks(float(sum(pts)), dist, "cuda")
     value = tot_pts / sum(times)
     ms = 1000.0 * sum(times) / len(times)
-    # roofline of the dominant kernel (HSS): algorithmic lane-ops / HSS time
-    zall = np.array(logz)
-    out_frac_est = 0.12
-    drawn_ahead = prof.get("noise_steps", 0) > 0
-    ops = lane_ops_per_point_step(32, 4, out_frac_est, rng=not drawn_ahead)
-    hss_s = prof["hss_ms"] / 1000.0  # time during which HSS kernels of any run were executing
-    achieved = ops * (sum(pts)) / hss_s if hss_s > 0 else None
+    peaks = load_peaks()
     f_sm = (clocks.get("sm_mhz") or 1447.0) * 1e6
-    peak = SMS * FP32_LANES_PER_SM * f_sm
-    hss_iters = max(prof["hss_iters"], 1)
-    roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
-            "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(),
-            "traffic_unit": "bytes per launch (DRAM read + write)",
-            "kernel": ("k_hss1 + k_hss_pick (single pass)" if prof.get("rec_len", 0) > 0 else "k_hss (phases 0-2)"),
-            "hss_rec_overflows": prof.get("rec_overflows"), "ops_per_point_step": ops,
-            "noise": ("drawn ahead by k_noise on a side stream (not in this kernel's count): "
-                      f"{lane_ops_per_point_step(32, 4, 0.0) - lane_ops_per_point_step(32, 4, 0.0, rng=False):.0f} "
-                      "lane-ops per point-step") if drawn_ahead else "drawn in the walk",
-            "hss_ms_per_run_iteration": prof["hss_ms_sum"] / hss_iters,
-            "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
-            "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}
-    # e2e: through the C ABI from host buffers (create = H2D of parameters, result = D2H)
-    e2e_t = []
+    hss_s = prof["hss_ms"] / 1000.0
+    if name == "c5":
+        d, K = 512, 8
+        flops = dense_mix_flops_per_point_step(d, K)
+        tensor = prof.get("tensor_classes", 0) > 0
+        achieved = flops * sum(pts) / hss_s if hss_s > 0 else None
+        if tensor:
+            # TF32 tcgen05: the measured BF16 peak (sustained: the kernel runs inside a long step)
+            # times the nominal TF32/BF16 ratio 1/2
+            peak = 0.5 * float(peaks.get("bf16_tflops_sustained") or 1700.0) * 1e12
+            bound, pnote = "tensor", "TF32 = measured BF16 sustained x 1/2 (nominal dtype ratio)"
+        else:
+            peak = SMS * FP32_LANES_PER_SM * 2.0 * f_sm
+            bound, pnote = "alu", f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {f_sm / 1e6:.0f} MHz"
+        roof = {"bound": bound, "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(name),
+                "kernel": "dense-mixture HSS walk (k_hss1, CTA-cooperative)", "flops_per_point_step": flops,
+                "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
+                "hss_ms_per_iteration": prof["hss_ms_sum"] / max(prof["hss_iters"], 1), "peak_note": pnote}
+    else:
+        ops = lane_ops_per_point_step(32, 4, 0.12, rng=not prof.get("noise_steps", 0) > 0)
+        achieved = ops * sum(pts) / hss_s if hss_s > 0 else None
+        peak = SMS * FP32_LANES_PER_SM * f_sm
+        roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
+                "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": measured_traffic(name), "kernel": "k_hss1 + k_hss_pick", "ops_per_point_step": ops,
+                "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
+                "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}
+    # e2e: through the C ABI from host buffers: create (H2D of the problem), run, results and the
+    # gradient read back (D2H)
     h2d = 0
     for r in runs:
         sp = r["spec"]
-        h2d += 8 * (2 * sp["d"] + np.size(sp["means"]) + np.size(sp["sigma"]) + np.size(sp.get("log_weights", [])))
-    d2h = R * 96
+        h2d += 8 * (2 * sp["d"] + np.size(sp["means"]) + np.size(sp.get("sigma", [])) +
+                    np.size(sp.get("log_weights", [])) + np.size(sp.get("precision", [])))
+    d2h = R * (96 + 8 * np.size(w["spec"]["means"]))
+    e2e_t = []
     for i in range(max(1, min(2, args.steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = ggns.Sampler(runs)
         s2.run()
         _ = [s2.result(r) for r in range(R)]
+        _ = [s2.grad_logz(r) for r in range(R)]
         s2.close()
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_pts = pts[-1]
-    e2e_value = e2e_pts / (sum(e2e_t) / len(e2e_t))
-    # the plain GPU path: one run per context, one host-synchronised launch chain per iteration
-    plain_ms = None
-    if not args.no_plain:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for r in runs:
-            sp = ggns.Sampler([r])
-            while not sp.step(1):
-                pass
-            sp.run(0)
-            sp.result(0)
-            sp.close()
-        torch.cuda.synchronize()
-        plain_ms = 1000.0 * (time.perf_counter() - t0)
+    e2e_value = pts[-1] / (sum(e2e_t) / len(e2e_t))
+    c2leg = None
+    if name == "c5" and world == 1 and not args.no_c2:
+        c2leg = _c2_time_to_logz(ggns, torch, stream, flush, rank, args.warmup)
     line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
-            threads = min(os.cpu_count() or 1, R)
-            n, t, _ = oracle_sample(threads, threads, seed_base=50_000)
+            threads = os.cpu_count() or 1
+            if name == "c2":
+                threads = min(threads, C2_REPLICAS)
+            n, t = oracle_sample(name, threads, seed_base=50_000)
             cpu = {"value": n / t, "unit": UNIT, "cores": threads, "kind": "oracle",
-                   "sample": f"{threads} complete oracle runs of the workload on {threads} host threads "
-                             f"({n} point-steps in {t:.1f} s)"}
+                   "sample": sample_note(name, threads, n, t)}
+        z = np.array(logz)
+        truth = W.truth_logz(w)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
-                "time_to_logz_ms": ms,
-                "plain": None if plain_ms is None else {
-                    "time_to_logz_ms": plain_ms,
-                    "what": "same replicas one after another, one context each, one host-synchronised launch "
-                            "chain per iteration (no graph, no batching)",
-                    "speedup": plain_ms / ms},
-                "logz_mean": float(zall.mean()), "logz_truth": truth,
-                "dlogz_mean": float(zall.mean() - truth), "logz_err_mean": float(np.mean(errs)),
-                "logz_sd": float(zall.std()),
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(name),
+                "logz_mean": float(z.mean()),
+                "logz_truth_box_mass_1": truth,
                 "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(prof["launches"] / max(args.steps, 1)),
                 "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
                            "reasons": clocks.get("reasons")},
-                "peaks": {k: load_peaks().get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+                "peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")}}
+        if c2leg is not None:
+            line["time_to_logz"] = c2leg
+        if name == "c2":
+            line["dlogz_mean"] = float(z.mean() - truth)
         print(json.dumps(line), flush=True)
     s.close()
     if dist is not None:
@@ -387,12 +481,12 @@ def gpu_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ggns", choices=["ggns", "reference"])
-    ap.add_argument("--replicas", type=int, default=DEFAULT_REPLICAS)
+    ap.add_argument("--workload", default="c5", choices=["c5", "c2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-c2", action="store_true", help="skip the c2x17 time-to-log-Z leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -113,10 +113,10 @@ typedef struct {
     int territory;     /* 1: with several clusters alive, a new point whose nearest surviving
                           point belongs to another cluster returns its start point               */
     int keep_last;     /* Appendix G ablation: 1 returns the last inside state of the window     */
-    int box_fold;      /* 1: the prior box reflects a walker exactly (its position folds back across
-                          the face, that momentum component flips; no outside step), so only the
-                          iso-likelihood boundary of Algorithm 5 counts as outside
-                          0: leaving the box is an outside step reflected off the violated faces */
+    int box_fold;      /* 0: leaving the prior box is an outside step, reflected off the violated faces
+                          1: the box reflects a walker exactly (its position folds back across the
+                          face, that momentum component flips; no outside step), so only the
+                          iso-likelihood boundary of Algorithm 5 counts as outside              */
     /* Launch choices; 0 selects the library's own choice.  Options marked (context) are read
      * from the first configuration of a batch; tile from the first run of each (kind, d).    */
     int tile;          /* walker tile id + 1: 1..N_TILES (G lanes x E components, ns_tile_shape) */
@@ -131,7 +131,7 @@ typedef struct {
  * delta_p 0.5, tol 0.01, min_ref 1, max_ref 3, prune_after 10, termination 0,
  * clustering 1, noise_mode 1, out_lo 0.05, out_hi 0.15, seed 0, run_id 0,
  * max_iters 100000, dead_cap 0, noise_inside 1, pick_all 1, territory 1,
- * keep_last 0, box_fold 1 and every launch choice 0 (the library's own). */
+ * keep_last 0, box_fold 0 and every launch choice 0 (the library's own). */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context for one run.  Copies the box, the likelihood parameters and
@@ -286,7 +286,9 @@ ns_status ns_knn_components(const float *x_dev, int m, int d, int *comp_dev, int
  * that every GPU loading the library holds until the process exits; the call
  * allocates and frees nothing.  The first call on a device, with that device
  * current, looks up the array's device address; make that first call before
- * any stream capture.  Every call reuses the same array and leaves its contents
+ * any stream capture.  The address is kept per driver context: after a device
+ * reset (or any new primary context) the next call looks it up again, so that
+ * call too should come before any stream capture.  Every call reuses the same array and leaves its contents
  * behind (each call re-initialises what it reads), so calls that overlap on the
  * GPU -- on different streams or host threads -- race and must be serialised
  * by the caller.  Synchronises `stream`. */

@@ -75,7 +75,7 @@ struct RunClass {
 // group, because concurrent groups share the SMs and the walkers of one group's
 // single-pass HSS then stop being co-resident.
 struct Group {
-    int r0 = 0, nr = 0, max_n = 0, max_k = 0, max_dpad = 0;
+    int r0 = 0, nr = 0, max_n = 0, max_k = 0, max_d = 0;
     std::vector<RunClass> classes;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -470,7 +470,7 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
         }
     // a new point that landed in another cluster's region returns its start point
     if (ctx->any_territory) {
-        CU(launch_territory(C, g.r0, g.nr, g.max_k, g.max_dpad, s));
+        CU(launch_territory(C, g.r0, g.nr, g.max_k, g.max_d, s));
         ++n;
     }
     // fork: the tail (step size, counters, iteration count), then the next iteration's noise
@@ -589,7 +589,7 @@ void ns_config_default(ns_config *c)
     c->noise_inside = 1;
     c->pick_all = 1;
     c->territory = 1;
-    c->box_fold = 1;
+    c->box_fold = 0;
 }
 
 const char *ns_last_error(const ns_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -845,7 +845,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                     const RunDesc &D = ctx->desc[r];
                     g.max_n = std::max(g.max_n, D.n_live);
                     g.max_k = std::max(g.max_k, D.k);
-                    g.max_dpad = std::max(g.max_dpad, D.d_pad);
+                    g.max_d = std::max(g.max_d, D.d);
                     auto key = std::make_pair(D.kind, D.tile);
                     if (!gcls.count(key)) {
                         gcls[key] = (int)g.classes.size();
@@ -1282,51 +1282,77 @@ ns_status ns_state_save(const ns_ctx *cctx, void *buf, size_t cap, size_t *n)
 ns_status ns_state_load(ns_ctx *ctx, const void *buf, size_t n)
 {
     if (!ctx || !buf || n < sizeof(SaveHeader)) return NS_ERR_ARG;
-    const char *p = static_cast<const char *>(buf);
+    const char *base = static_cast<const char *>(buf);
     SaveHeader h;
-    memcpy(&h, p, sizeof h);
-    p += sizeof h;
-    if (h.magic != 0x474753535441ull || h.n_runs != ctx->n_runs || h.fa_len != ctx->fa_len || h.pt_len != ctx->pt_len)
+    memcpy(&h, base, sizeof h);
+    if (h.magic != 0x474753535441ull || h.n_runs != ctx->n_runs || h.fa_len != ctx->fa_len || h.pt_len != ctx->pt_len ||
+        h.w_len != ctx->w_len)
         return fail(ctx, NS_ERR_ARG, "ns_state_load: state does not match this context");
-    const char *end = static_cast<const char *>(buf) + n;
-    auto h2d = [&](void *dst, size_t bytes) -> ns_status {
-        if (p + bytes > end) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
-        CU(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
-        p += bytes;
+    // Parse and check the whole buffer on the host before anything reaches the device:
+    // on any error the context keeps its previous state.
+    const int R = ctx->n_runs;
+    size_t off = sizeof h;
+    const size_t off_state = off;
+    off += sizeof(RunState) * R;
+    const size_t off_stats = off;
+    off += sizeof(Stats) * R;
+    const size_t off_fa = off;
+    off += sizeof(float) * ctx->fa_len;
+    const size_t off_pt = off;
+    off += (sizeof(float) + 2 * sizeof(int)) * ctx->pt_len;
+    if (off > n) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
+    std::vector<RunState> st(R);
+    memcpy(st.data(), base + off_state, sizeof(RunState) * R);
+    std::vector<size_t> off_dead(R);
+    std::vector<long> nds(R);
+    for (int r = 0; r < R; ++r) {
+        long nd;
+        if (off + sizeof nd > n) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
+        memcpy(&nd, base + off, sizeof nd);
+        off += sizeof nd;
+        const RunDesc &D = ctx->desc[r];
+        const size_t row = sizeof(float) * D.d_pad + sizeof(float) + sizeof(double) + sizeof(int);
+        if (nd < 0 || (size_t)nd > (n - off) / row) return fail(ctx, NS_ERR_ARG, "ns_state_load: bad dead-point count");
+        const RunState &S = st[r];
+        if (S.n_dead != nd || S.dead_base < 0 || S.dead_base > nd || S.n_clusters < 0 || S.n_clusters > CMAX ||
+            S.iter < 0)
+            return fail(ctx, NS_ERR_ARG, "ns_state_load: run %d: inconsistent run state", r);
+        nds[r] = nd;
+        off_dead[r] = off;
+        off += (size_t)nd * row;
+    }
+    if (off != n) return fail(ctx, NS_ERR_ARG, "ns_state_load: %zu bytes given, the state holds %zu", n, off);
+    ns_status s;
+    // room for the dead rows (and the iterations that follow) before the copies
+    for (int r = 0; r < R; ++r) {
+        const long need = nds[r] + ctx->desc[r].n_live + (long)GRAPH_ITERS * ctx->desc[r].k;
+        if (need > ctx->desc[r].dead_cap && (s = alloc_dead(ctx, r, need)) != NS_OK) return s;
+    }
+    auto h2d = [&](void *dst, size_t at, size_t bytes) -> ns_status {
+        CU(cudaMemcpyAsync(dst, base + at, bytes, cudaMemcpyHostToDevice, ctx->stream));
         return NS_OK;
     };
-    ns_status s;
-    std::vector<RunState> st(ctx->n_runs);
-    if (p + sizeof(RunState) * ctx->n_runs > end) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
-    memcpy(st.data(), p, sizeof(RunState) * ctx->n_runs);
-    if ((s = h2d(ctx->state_dev, sizeof(RunState) * ctx->n_runs)) != NS_OK) return s;
-    if ((s = h2d(ctx->stats_dev, sizeof(Stats) * ctx->n_runs)) != NS_OK) return s;
+    if ((s = h2d(ctx->state_dev, off_state, sizeof(RunState) * R)) != NS_OK) return s;
+    if ((s = h2d(ctx->stats_dev, off_stats, sizeof(Stats) * R)) != NS_OK) return s;
     // keep this context's parameter block layout: the float arena holds live x, walker state, parameters
-    if ((s = h2d(ctx->fa, sizeof(float) * ctx->fa_len)) != NS_OK) return s;
-    if ((s = h2d(ctx->logl, sizeof(float) * ctx->pt_len)) != NS_OK) return s;
-    if ((s = h2d(ctx->label, sizeof(int) * ctx->pt_len)) != NS_OK) return s;
-    if ((s = h2d(ctx->order, sizeof(int) * ctx->pt_len)) != NS_OK) return s;
-    CU(cudaStreamSynchronize(ctx->stream));
-    for (int r = 0; r < ctx->n_runs; ++r) {
-        long nd;
-        if (p + sizeof nd > end) return fail(ctx, NS_ERR_ARG, "ns_state_load: truncated state");
-        memcpy(&nd, p, sizeof nd);
-        p += sizeof nd;
-        if (nd < 0 || nd > (long)((end - p) / sizeof(float)))
-            return fail(ctx, NS_ERR_ARG, "ns_state_load: bad dead-point count");
-        if (nd + ctx->desc[r].n_live + (long)GRAPH_ITERS * ctx->desc[r].k > ctx->desc[r].dead_cap) {
-            // grow this run's arena before copying its rows in
-            RunState zero = st[r];
-            zero.n_dead = 0;
-            CU(cudaMemcpy(ctx->state_dev + r, &zero, sizeof zero, cudaMemcpyHostToDevice));
-            if ((s = alloc_dead(ctx, r, nd + ctx->desc[r].n_live + (long)GRAPH_ITERS * ctx->desc[r].k)) != NS_OK) return s;
-            CU(cudaMemcpy(ctx->state_dev + r, &st[r], sizeof(RunState), cudaMemcpyHostToDevice));
-        }
+    if ((s = h2d(ctx->fa, off_fa, sizeof(float) * ctx->fa_len)) != NS_OK) return s;
+    size_t o = off_pt;
+    if ((s = h2d(ctx->logl, o, sizeof(float) * ctx->pt_len)) != NS_OK) return s;
+    o += sizeof(float) * ctx->pt_len;
+    if ((s = h2d(ctx->label, o, sizeof(int) * ctx->pt_len)) != NS_OK) return s;
+    o += sizeof(int) * ctx->pt_len;
+    if ((s = h2d(ctx->order, o, sizeof(int) * ctx->pt_len)) != NS_OK) return s;
+    for (int r = 0; r < R; ++r) {
         const RunDesc &D = ctx->desc[r];
-        if ((s = h2d(D.dead_x, sizeof(float) * (size_t)nd * D.d_pad)) != NS_OK) return s;
-        if ((s = h2d(D.dead_logl, sizeof(float) * (size_t)nd)) != NS_OK) return s;
-        if ((s = h2d(D.dead_logw, sizeof(double) * (size_t)nd)) != NS_OK) return s;
-        if ((s = h2d(D.dead_label, sizeof(int) * (size_t)nd)) != NS_OK) return s;
+        const size_t nd = (size_t)nds[r];
+        size_t q = off_dead[r];
+        if ((s = h2d(D.dead_x, q, sizeof(float) * nd * D.d_pad)) != NS_OK) return s;
+        q += sizeof(float) * nd * D.d_pad;
+        if ((s = h2d(D.dead_logl, q, sizeof(float) * nd)) != NS_OK) return s;
+        q += sizeof(float) * nd;
+        if ((s = h2d(D.dead_logw, q, sizeof(double) * nd)) != NS_OK) return s;
+        q += sizeof(double) * nd;
+        if ((s = h2d(D.dead_label, q, sizeof(int) * nd)) != NS_OK) return s;
     }
     CU(cudaStreamSynchronize(ctx->stream));
     return NS_OK;

@@ -691,6 +691,11 @@ __device__ void sort_body(DevCtx C, int r, unsigned char *sraw)
     }
     if (tid == 0) {
         S->lstar = (double)logl[ordr[k - 1]];
+        if (!(S->lstar == S->lstar)) {
+            // more than half the live points have a NaN log-likelihood: no slice to sample
+            S->status = NS_ERR_NUMERIC;
+            S->done = 1;
+        }
         S->dead_base = dbase;
         S->n_dead = dbase + k;
         S->ev_pending = 1;
@@ -932,95 +937,128 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
 // Cluster regions of the new points (the bookkeeping of Appendix H holds when
 // the live points of a cluster lie in that cluster's region only)
 // ------------------------------------------------------------------------
-// The nearest of m candidate rows (FP32 squared distance accumulated over the d
-// coordinates in order by fused multiply-add; ties to the lower candidate key)
-// to the point q held in shared memory.  One warp; lane l scans candidates l,
-// l + 32, ...; returns the winning candidate position in every lane.
-// cand(i) gives the row of candidate i and key(i) its tie-break key.
+// Nearest-survivor search, one query per lane: a CTA of TER_WARPS warps serves 32
+// queries (new points) held transposed in shared memory (q[c * 33 + lane], no bank
+// conflicts); warp w scans the candidates w, w + TER_WARPS, ..., each candidate row
+// read once per warp as a broadcast, so a (query, candidate) pair costs one shared
+// load, one subtraction and one fused multiply-add per coordinate.  Squared
+// distances accumulate over the coordinates in order (FP32, round to nearest), the
+// order the oracle uses; ties go to the lower candidate key.  Returns, in every
+// lane of warp 0, the key of its query's nearest candidate (-1 if none).
+constexpr int TER_WARPS = 4;
+
 template <typename RowF, typename KeyF>
-__device__ __forceinline__ int warp_nearest(const float *q, int d, int m, RowF cand, KeyF key)
+__device__ __forceinline__ int tile_nearest(const float *q, int d, int m, RowF cand, KeyF key, float *mb, int *mk)
 {
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float best = INFINITY;
-    int bi = -1, bk = 0x7fffffff;
-    for (int i = lane; i < m; i += 32) {
+    int bk = 0x7fffffff;
+    for (int i = warp; i < m; i += TER_WARPS) {
         const float *row = cand(i);
         float s = 0.f;
         for (int c = 0; c < d; ++c) {
-            const float diff = q[c] - row[c];
+            const float diff = q[c * 33 + lane] - __ldg(row + c);
             s = __fmaf_rn(diff, diff, s);
         }
         const int k = key(i);
         if (s < best || (s == best && k < bk)) {
             best = s;
-            bi = i;
             bk = k;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-        if (ob < best || (ob == best && ok < bk)) {
-            best = ob;
-            bi = oi;
-            bk = ok;
+    mb[warp * 32 + lane] = best;
+    mk[warp * 32 + lane] = bk;
+    __syncthreads();
+    if (warp == 0) {
+        for (int w = 1; w < TER_WARPS; ++w) {
+            const float ob = mb[w * 32 + lane];
+            const int ok = mk[w * 32 + lane];
+            if (ob < best || (ob == best && ok < bk)) {
+                best = ob;
+                bk = ok;
+            }
         }
     }
-    return bi;
+    return bk == 0x7fffffff ? -1 : bk;
 }
 
-constexpr int TER_WARPS = 4;
+// Shared memory of the territory kernels: the query tile and the warps' partial minima.
+__host__ __device__ inline size_t territory_smem_bytes(int d)
+{
+    return sizeof(float) * (size_t)d * 33 + (sizeof(float) + sizeof(int)) * TER_WARPS * 32;
+}
 
 // Walker w's new point (slot order[w]) stays only if its nearest surviving point
 // (slots order[k .. n_live), ties to the lower slot) carries the label it was
 // spawned with; otherwise the slot takes the walker's start point and its log L.
-// Runs with clustering and the territory rule on; skipped when every survivor has
-// the new point's label (one cluster alive).
+// Runs with clustering and the region rule on; skipped while every survivor has
+// one label (the spawned label is always a survivor's).
 __global__ void __launch_bounds__(TER_WARPS * 32) k_territory(DevCtx C, int r0)
 {
     extern __shared__ float tsm[];
+    __shared__ int s_mixed;
     const int r = r0 + blockIdx.y;
     const RunDesc &D = C.desc[r];
     const RunState *S = C.state + r;
     if (S->done || !D.clustering || !D.territory) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x * TER_WARPS + warp;
-    if (w >= D.k) return;
     const int n = D.n_live, k = D.k, dp = D.d_pad, d = D.d;
+    const int w0 = blockIdx.x * 32;
+    if (w0 >= k) return;
     const int *ord = C.order + D.pt_off;
-    const int want = C.new_label[D.w_off + w];
-    bool other = false;
-    for (int i = k + lane; i < n; i += 32) other |= (C.label[D.pt_off + ord[i]] != want);
-    if (!__any_sync(0xffffffffu, other)) return;
-    const int slot = ord[w];
-    float *q = tsm + (long)warp * dp;
+    const int *lab = C.label + D.pt_off;
+    if (threadIdx.x == 0) s_mixed = 0;
+    __syncthreads();
+    const int l0 = lab[ord[k]];
+    bool mixed = false;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) mixed |= (lab[ord[i]] != l0);
+    if (mixed) s_mixed = 1;
+    __syncthreads();
+    if (!s_mixed) return;
     const float *xs = C.fa + D.x_off;
-    for (int c = lane; c < dp; c += 32) q[c] = xs[(long)slot * dp + c];
-    __syncwarp();
-    const int bi = warp_nearest(q, d, n - k, [&](int i) { return xs + (long)ord[k + i] * dp; },
-                                [&](int i) { return ord[k + i]; });
-    if (bi < 0 || C.label[D.pt_off + ord[k + bi]] == want) return;
-    const int s0 = C.start_slot[D.w_off + w];
-    for (int c = lane; c < dp; c += 32) C.fa[D.x_off + (long)slot * dp + c] = xs[(long)s0 * dp + c];
-    if (lane == 0) C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
+    float *q = tsm;
+    float *mb = tsm + (size_t)d * 33;
+    int *mk = reinterpret_cast<int *>(mb + TER_WARPS * 32);
+    for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
+        const int j = e / d, c = e - j * d;
+        q[c * 33 + j] = (w0 + j < k) ? xs[(long)ord[w0 + j] * dp + c] : 0.f;
+    }
+    __syncthreads();
+    const int near = tile_nearest(q, d, n - k, [&](int i) { return xs + (long)ord[k + i] * dp; },
+                                  [&](int i) { return ord[k + i]; }, mb, mk);
+    const int lane = threadIdx.x & 31, w = w0 + lane;
+    const bool reject = (threadIdx.x < 32) && w < k && near >= 0 && lab[near] != C.new_label[D.w_off + w];
+    // the warps copy the rejected walkers' start points
+    __shared__ int s_rej[32];
+    if (threadIdx.x < 32) s_rej[lane] = reject ? 1 : 0;
+    __syncthreads();
+    for (int j = 0; j < 32; ++j) {
+        if (!s_rej[j]) continue;
+        const int ww = w0 + j;
+        const int slot = ord[ww], s0 = C.start_slot[D.w_off + ww];
+        for (int c = threadIdx.x; c < dp; c += blockDim.x) C.fa[D.x_off + (long)slot * dp + c] = xs[(long)s0 * dp + c];
+        if (threadIdx.x == 0) C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
+    }
 }
 
 // Component form for the tests: keep[j] = 1 if the nearest of the m_s survivor
 // rows surv[m_s][d] (ties to the lower row) to xn[j] carries label want[j].
-__global__ void k_territory_plain(const float *surv, const int *surv_label, int m_s, const float *xn,
-                                  const int *want, int k, int d, int *keep)
+__global__ void __launch_bounds__(TER_WARPS * 32) k_territory_plain(const float *surv, const int *surv_label, int m_s,
+                                                                    const float *xn, const int *want, int k, int d,
+                                                                    int *keep)
 {
     extern __shared__ float tsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * TER_WARPS + warp;
-    if (j >= k) return;
-    float *q = tsm + (long)warp * d;
-    for (int c = lane; c < d; c += 32) q[c] = xn[(long)j * d + c];
-    __syncwarp();
-    const int bi = warp_nearest(q, d, m_s, [&](int i) { return surv + (long)i * d; }, [&](int i) { return i; });
-    if (lane == 0) keep[j] = (bi < 0 || surv_label[bi] == want[j]) ? 1 : 0;
+    const int w0 = blockIdx.x * 32;
+    float *q = tsm;
+    float *mb = tsm + (size_t)d * 33;
+    int *mk = reinterpret_cast<int *>(mb + TER_WARPS * 32);
+    for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
+        const int j = e / d, c = e - j * d;
+        q[c * 33 + j] = (w0 + j < k) ? xn[(long)(w0 + j) * d + c] : 0.f;
+    }
+    __syncthreads();
+    const int near = tile_nearest(q, d, m_s, [&](int i) { return surv + (long)i * d; }, [&](int i) { return i; }, mb, mk);
+    const int j = w0 + threadIdx.x;
+    if (threadIdx.x < 32 && j < k) keep[j] = (near < 0 || surv_label[near] == want[j]) ? 1 : 0;
 }
 
 // ------------------------------------------------------------------------
@@ -1881,18 +1919,28 @@ cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k,
     k_hss_pick<<<dim3((max_k + PICK_WARPS - 1) / PICK_WARPS, nr), PICK_WARPS * 32, 0, s>>>(C, runs, R, rec_base);
     return cudaGetLastError();
 }
-cudaError_t launch_territory(const DevCtx &C, int r0, int n_runs, int max_k, int max_dpad, cudaStream_t s)
+cudaError_t launch_territory(const DevCtx &C, int r0, int n_runs, int max_k, int max_d, cudaStream_t s)
 {
-    k_territory<<<dim3((max_k + TER_WARPS - 1) / TER_WARPS, n_runs), TER_WARPS * 32,
-                  sizeof(float) * TER_WARPS * max_dpad, s>>>(C, r0);
+    const size_t smem = territory_smem_bytes(max_d);
+    static size_t opted = 48 * 1024;
+    if (smem > opted) {
+        cudaError_t e = cudaFuncSetAttribute(k_territory, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
+    k_territory<<<dim3((max_k + 31) / 32, n_runs), TER_WARPS * 32, smem, s>>>(C, r0);
     return cudaGetLastError();
 }
 cudaError_t launch_territory_plain(const float *surv, const int *surv_label, int m_s, const float *xn, const int *want,
                                    int k, int d, int *keep, cudaStream_t s)
 {
     if (k <= 0) return cudaSuccess;
-    k_territory_plain<<<(k + TER_WARPS - 1) / TER_WARPS, TER_WARPS * 32, sizeof(float) * TER_WARPS * d, s>>>(
-        surv, surv_label, m_s, xn, want, k, d, keep);
+    const size_t smem = territory_smem_bytes(d);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_territory_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_territory_plain<<<(k + 31) / 32, TER_WARPS * 32, smem, s>>>(surv, surv_label, m_s, xn, want, k, d, keep);
     return cudaGetLastError();
 }
 cudaError_t launch_term_cluster_sort(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,

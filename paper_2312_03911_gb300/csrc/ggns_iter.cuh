@@ -29,7 +29,7 @@ cudaError_t launch_noise(const DevCtx &C, const int *runs, int nr, int blocks_pe
 cudaError_t launch_hss_pick(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                             const long *rec_base, cudaStream_t s);
 cudaError_t launch_term(const DevCtx &C, int r0, int n_runs, cudaStream_t s);
-cudaError_t launch_territory(const DevCtx &C, int r0, int n_runs, int max_k, int max_dpad, cudaStream_t s);
+cudaError_t launch_territory(const DevCtx &C, int r0, int n_runs, int max_k, int max_d, cudaStream_t s);
 cudaError_t launch_territory_plain(const float *surv, const int *surv_label, int m_s, const float *xn, const int *want,
                                    int k, int d, int *keep, cudaStream_t s);
 cudaError_t launch_term_cluster_sort(const DevCtx &C, int r0, int n_runs, unsigned long long *lastkey, size_t smem,

@@ -42,6 +42,27 @@ __global__ void k_noalloc_reset(KnnScratch *s, int m)
 constexpr int MAX_DEVICES = 256;
 std::mutex g_mu;
 KnnScratch *g_dev_ptr[MAX_DEVICES] = {};
+void *g_dev_ctx[MAX_DEVICES] = {};  // the context the address was looked up in
+
+// The current driver context, through the runtime's driver entry point (no link to
+// libcuda); nullptr if it cannot be queried.  A device reset or a new primary
+// context reloads the module and moves the array, so the cached address is kept
+// per context, not per device.
+void *current_context()
+{
+    using GetCtx = int (*)(void **);
+    static GetCtx fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetCtx>(f);
+    }();
+    void *c = nullptr;
+    if (!fn || fn(&c) != 0) return nullptr;
+    return c;
+}
 
 }  // namespace
 
@@ -67,7 +88,8 @@ extern "C" ns_status ns_knn_components_noalloc(const float *x_dev, int m, int d,
         // set-up, once per device with that device current: the device address of
         // the scratch (the host-side name is only a stand-in for it)
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_dev_ptr[dev]) {
+        void *cur = current_context();
+        if (!g_dev_ptr[dev] || !cur || cur != g_dev_ctx[dev]) {
             void *addr = nullptr;
             e = cudaGetSymbolAddress(&addr, g_knn_scratch);
             if (e != cudaSuccess) {
@@ -75,6 +97,7 @@ extern "C" ns_status ns_knn_components_noalloc(const float *x_dev, int m, int d,
                 return NS_ERR_CUDA;
             }
             g_dev_ptr[dev] = static_cast<KnnScratch *>(addr);
+            g_dev_ctx[dev] = current_context();
         }
         p = g_dev_ptr[dev];
     }

@@ -36,17 +36,16 @@ LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN, LIK_TORUS = 0, 1, 2, 
 # inside steps only (an outside step only reflects); each walker's pick is uniform
 # over the steps of its saving window, a drawn outside step returning the start
 # point; with several clusters alive a new point that lands nearer another
-# cluster's survivors returns its start point; the prior box reflects a walker
-# exactly (position folded back, momentum component flipped), so only the
-# iso-likelihood boundary counts as outside.  The printed forms (multiplicative
-# noise with dp = 0.05 on every step, the pick among inside states only) remain
-# selectable: PAPER_NOISE and PRINTED_PICK.
+# cluster's survivors returns its start point.  Leaving the prior box is an
+# outside step (box_fold = 1, an exact reflection off the faces, is an option).
+# The printed forms (multiplicative noise with dp = 0.05 on every step, the pick
+# among inside states only) remain selectable: PAPER_NOISE and PRINTED_PICK.
 DEFAULT_CFG = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.5, tol=0.01, min_ref=1,
                    max_ref=3, prune_after=10, termination=0, clustering=1, seed=0, run_id=0,
                    max_iters=100000, noise_mode=1, out_lo=0.05, out_hi=0.15, noise_inside=1, pick_all=1,
-                   territory=1, box_fold=1)
+                   territory=1, box_fold=0)
 PAPER_NOISE = dict(noise_mode=0, delta_p=0.05, noise_inside=0)
-PRINTED_PICK = dict(pick_all=0, territory=0, box_fold=0)
+PRINTED_PICK = dict(pick_all=0, territory=0)
 
 
 def _rng(seed):

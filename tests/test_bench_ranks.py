@@ -22,7 +22,7 @@ def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        _, runs = bench.replicas(3, rank)
+        _, runs = bench.runs_of("c2", 3, rank)
         ids = [r["cfg"]["run_id"] for r in runs]
         t = bench.max_over_ranks(1.0 + rank, dist, "cpu")
         n = bench.sum_over_ranks(10.0 * (rank + 1), dist, "cpu")

@@ -1,0 +1,111 @@
+"""GPU side of the Appendix G ablations and of the mode-finding test, against the oracle.
+
+Every variant runs as a batch of seeded replicas on the GPU and as seeded oracle runs of the
+same configuration; the means of log Z (and the mode counts) must agree statistically.  The
+ablations themselves are expected to be biased (that is the paper's point); the test is that
+the library and the oracle implement the same variant."""
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_03911_gb300 import ggns
+from paper_2312_03911_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_03911_gb300 import build
+    build.build()
+    ggns.load()
+
+
+def _gpu(w, R):
+    s = ggns.Sampler([dict(w, cfg=dict(w["cfg"], run_id=r)) for r in range(R)])
+    s.run()
+    res = [s.result(r, check=False) for r in range(R)]
+    return s, res
+
+
+def _orc(w, run_ids):
+    lik = oracle.Likelihood.from_spec(w["spec"])
+
+    def one(r):
+        return oracle.run(lik, w["lo"], w["hi"], oracle.make_cfg(**dict(w["cfg"], run_id=r)))
+
+    with ThreadPoolExecutor(max_workers=min(len(run_ids), os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, run_ids))
+
+
+def _agree(zg, zo, floor):
+    se = math.sqrt(np.var(zg, ddof=1) / len(zg) + np.var(zo, ddof=1) / len(zo))
+    return abs(np.mean(zg) - np.mean(zo)) < max(floor, 4 * se), (np.mean(zg), np.mean(zo), se)
+
+
+# (name, configuration overrides): Appendix G's fixed step sizes, no momentum noise, the classic
+# termination, the fixed-step keep-last sampler, and Algorithm 5's printed noise and pick
+VARIANTS = [
+    ("fixed dt 0.1", dict(dt_init=0.1, out_lo=0.0, out_hi=1.0)),
+    ("fixed dt 0.5", dict(dt_init=0.5, out_lo=0.0, out_hi=1.0)),
+    ("no noise", dict(delta_p=0.0)),
+    ("classic termination", dict(termination=1, tol=0.01)),
+    ("keep last, 20 steps", dict(keep_last=1, n_steps=20, min_steps=20, min_ref=0, max_ref=10**6)),
+    ("printed noise", dict(noise_mode=0, delta_p=0.05)),
+    ("printed noise and pick", dict(noise_mode=0, delta_p=0.05, noise_inside=0, pick_all=0, territory=0)),
+    ("exact box reflection", dict(box_fold=1)),
+]
+
+
+@pytest.mark.parametrize("name,over", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_ablation_variant_matches_oracle(name, over):
+    w = W.small_workload("iso", 8, 200, seed=4)
+    w = dict(w, cfg=dict(w["cfg"], **over))
+    s, res = _gpu(w, 16)
+    assert all(r["status"] == 0 for r in res), [r["status"] for r in res]
+    zg = np.array([r["logz"] for r in res])
+    zo = np.array([o["logz"] for o in _orc(w, list(range(100, 108)))])
+    ok, info = _agree(zg, zo, 0.25)
+    assert ok, (name, info)
+    # the likelihood evaluations per run agree too (same trajectory rules on both sides)
+    ng = np.mean([r["n_like"] for r in res])
+    no = np.mean([o["n_like"] for o in _orc(w, [100, 101])])
+    assert 0.7 < ng / no < 1.4, (name, ng, no)
+
+
+GRID = np.array([[a, b] for a in (-0.6, 0.0, 0.6) for b in (-0.6, 0.0, 0.6)])
+SIG = 0.05
+
+
+def _modes_found(x, lp):
+    """Modes holding at least a quarter of their share (1/9) of the posterior mass within 3 sigma."""
+    p = np.exp(lp - lp.max())
+    p /= p.sum()
+    near = np.linalg.norm(x[:, None, :] - GRID[None], axis=2) < 3 * SIG
+    mass = np.array([p[near[:, k]].sum() for k in range(len(GRID))])
+    return int((mass > 0.25 / len(GRID)).sum())
+
+
+@pytest.mark.parametrize("clustering,n_live", [(1, 50), (0, 50), (1, 200)])
+def test_mode_finding_matches_oracle(clustering, n_live):
+    """The nine-Gaussian grid (Appendix G's mode-collapse test, 10 runs): the mean number of
+    modes found on the GPU matches the oracle's within 1.5 modes, with clustering on and off."""
+    spec = dict(kind=W.LIK_MIX_ISO, d=2, means=GRID, sigma=np.full(9, SIG), log_weights=np.full(9, -math.log(9)))
+    cfg = dict(W.DEFAULT_CFG, n_live=n_live, termination=1, tol=1e-3, clustering=clustering, seed=91)
+    w = dict(spec=spec, lo=-np.ones(2), hi=np.ones(2), cfg=cfg)
+    s, res = _gpu(w, 10)
+    assert all(r["status"] == 0 and r["terminated"] == 1 for r in res)
+    fg = [_modes_found(*s.samples(r)) for r in range(10)]
+    orc = _orc(w, list(range(10)))
+    fo = [_modes_found(o["dead_x"], o["dead_logw"] + o["dead_logl"] - o["logz"]) for o in orc]
+    assert abs(np.mean(fg) - np.mean(fo)) < 1.5, (fg, fo)
+    if n_live == 200 and clustering:
+        assert np.mean(fg) >= 8.5
