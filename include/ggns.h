@@ -123,7 +123,9 @@ typedef struct {
     int hss_mode;      /* (context) 1: single pass where resident; 2: three phases always        */
     int rec_len;       /* (context) step records per walker of the single pass (0: n_steps)     */
     int noise_ahead;   /* (context) steps of momentum noise drawn ahead (0: 128; -1: none)       */
-    int coop;          /* (context) dense walk sharing P tiles per CTA: 0 auto, -1 off          */
+    int coop;          /* (context) dense walk, 16 walkers per CTA sharing each read of P: 0 with
+                          the contraction on the tensor cores where d_pad is 128, 256 or 512,
+                          else on CUDA cores; 1 on CUDA cores; -1 off (one read per walker)     */
     int runs_per_group;/* (context) runs per concurrent group and graph (0: all in one group)    */
 } ns_config;
 
@@ -170,7 +172,7 @@ ns_status ns_run(ns_ctx *ctx, long max_iters);
  * Used to repeat a workload without allocating.  Synchronises. */
 ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
 
-/* Profiling counters of ctx (out[9]): out[0] milliseconds during which at
+/* Profiling counters of ctx (out[10]): out[0] milliseconds during which at
  * least one HSS kernel of ns_run was executing (union over the run groups of
  * the intervals between CUDA events recorded around the HSS kernels of each
  * iteration), out[1] group-iterations measured, out[2] kernels launched by
@@ -180,7 +182,8 @@ ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
  * out[6] step records per walker (0: the three-phase form only), out[7] steps
  * of momentum noise drawn ahead per walker (0: drawn during the walk), out[8]
  * walker classes stepping CTA-cooperatively (dense likelihoods whose precision
- * matrix is read from global memory in shared tiles).
+ * matrix is read from global memory in shared tiles), out[9] those of them whose
+ * contraction runs on the tensor cores (tcgen05, 3xTF32).
  * reset != 0 zeroes out[0..4] after reading.  Synchronises. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ggns_iter.cuh"
+#include "ggns_tc.cuh"
 #include "ggns_kernels.cuh"
 
 using namespace ggns;
@@ -65,7 +66,8 @@ struct RunClass {
     int prec_in_smem = 0;
     int single = 0;    // HSS in one pass (every walker block resident at once)
     int fallback = 1;  // three-phase kernels after the single pass (records shorter than n_steps)
-    int coop = 0;      // dense kinds with P outside shared memory: the CTA-cooperative single pass
+    int coop = 0;      // dense kinds with P outside shared memory, the CTA-cooperative single pass:
+                       // 1 contraction on CUDA cores, 2 on the tensor cores
     int coop_tr = 0;   // rows of P per shared-memory tile
     size_t coop_smem = 0;
 };
@@ -312,6 +314,32 @@ ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int 
                     for (int j = 0; j < d; ++j) s += lk.precision[(size_t)i * d + j] * lk.means[(size_t)k * d + j];
                     out[L.pmu + (long)k * d_pad + i] = (float)s;
                 }
+        }
+        if (tc_layout(lk.kind, d_pad)) {
+            // P = P_hi + P_lo, both TF32 (10-bit mantissas, rounded to nearest, ties away from
+            // zero); K-step j of 8 columns holds, for each 128-row tile m, the rows in core
+            // matrices of 8 rows x 4 columns: row r, column kk at (r/8) 64 + (kk/4) 32 + (r%8) 4 + kk%4
+            auto tf32 = [](float v) {
+                uint32_t u;
+                memcpy(&u, &v, 4);
+                u = (u + 0x1000u) & 0xFFFFE000u;
+                float r;
+                memcpy(&r, &u, 4);
+                return r;
+            };
+            const int mt = d_pad / 128, ks = d_pad / 8;
+            for (int j = 0; j < ks; ++j)
+                for (int m = 0; m < mt; ++m)
+                    for (int r = 0; r < 128; ++r)
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const int row = m * 128 + r, col = 8 * j + kk;
+                            const float p = (row < d && col < d) ? (float)lk.precision[(size_t)row * d + col] : 0.f;
+                            const float hi = tf32(p), lo = tf32(p - hi);
+                            const long at = (r / 8) * 64 + (kk / 4) * 32 + (r % 8) * 4 + (kk % 4);
+                            const long blk = (long)j * 2 * mt * 1024;
+                            out[L.ptc + blk + (long)m * 1024 + at] = hi;
+                            out[L.ptc + blk + (long)mt * 1024 + (long)m * 1024 + at] = lo;
+                        }
         }
     }
     return NS_OK;
@@ -872,11 +900,13 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                         rc.single = blocks <= (long)per_sm * n_sm ? 1 : 0;
                         rc.fallback = 0;
                         for (int r : rc.runs) rc.fallback |= (ctx->rec.rec_len < cfg[r].n_steps);
-                        // dense likelihoods whose P stays in global memory: walkers of a CTA share each
-                        // tile of P (coop = -1 keeps one read of P per walker-step)
+                        // dense likelihoods whose P stays in global memory: the walkers of a CTA share
+                        // each tile of P, with the contraction on the tensor cores (coop 0) or on CUDA
+                        // cores (coop 1); coop = -1 keeps one read of P per walker-step
                         const bool want = cfg[0].coop >= 0;
                         const bool dense = rc.kind == NS_LIK_DENSE_GAUSS || rc.kind == NS_LIK_DENSE_MIX;
-                        if (want && dense && !rc.prec_in_smem && !rc.fallback &&
+                        // (the tensor-core form also where P would fit in shared memory: d_pad = 128)
+                        if (want && dense && (!rc.prec_in_smem || cfg[0].coop == 0) && !rc.fallback &&
                             (rc.tile == 6 || rc.tile == 7 || rc.tile == 8)) {
                             size_t par = 0;
                             int dpm = 0;
@@ -888,14 +918,26 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
                                 const ParLayout Lr = par_layout(Dr.d, Dr.d_pad, Dr.n_comp, Dr.kind);
                                 aligned &= ((Dr.par_off + Lr.prec) % 4) == 0;
                             }
+                            const long cb = (rc.max_k + COOP_THREADS / 32 - 1) / (COOP_THREADS / 32) *
+                                            (long)rc.runs.size();
+                            // the contraction on the tensor cores (coop = 0, the default)
+                            if (cfg[0].coop == 0 && aligned && tc_layout(rc.kind, dpm)) {
+                                const size_t need = 4 * par + tc::plan(dpm).total + 1024;
+                                int cps = 0;
+                                if (need <= COOP_SMEM_LIMIT) CU(kind_launch(rc.kind).hss1_coop_occ(rc.tile, need, 0, &cps));
+                                if (need <= COOP_SMEM_LIMIT && cps > 0 && cb <= (long)cps * n_sm) {
+                                    rc.coop = 2;
+                                    rc.coop_tr = 0;
+                                    rc.coop_smem = need;
+                                    rc.single = 1;
+                                }
+                            }
                             const size_t base = 4 * (par + (size_t)(COOP_THREADS / 32) * dpm) + 16;
-                            for (int tr = 64; tr >= 8 && aligned; tr /= 2) {
+                            for (int tr = 64; tr >= 8 && aligned && rc.coop == 0 && !rc.prec_in_smem; tr /= 2) {
                                 const size_t need = base + 2 * 4 * (size_t)tr * dpm;
                                 if (need > COOP_SMEM_LIMIT) continue;
                                 int cps = 0;
-                                CU(kind_launch(rc.kind).hss1_coop_occ(rc.tile, need, &cps));
-                                const long cb = (rc.max_k + COOP_THREADS / 32 - 1) / (COOP_THREADS / 32) *
-                                                (long)rc.runs.size();
+                                CU(kind_launch(rc.kind).hss1_coop_occ(rc.tile, need, tr, &cps));
                                 if (cps > 0 && cb <= (long)cps * n_sm) {
                                     rc.coop = 1;
                                     rc.coop_tr = tr;
@@ -1124,10 +1166,14 @@ ns_status ns_profile(const ns_ctx *cctx, double *out, int reset)
     out[5] = (double)over;
     out[6] = ctx->rec.rec_len;
     out[7] = ctx->rec.nT;
-    int ncoop = 0;
+    int ncoop = 0, ntc = 0;
     for (auto &g : ctx->groups)
-        for (auto &cl : g.classes) ncoop += cl.coop;
+        for (auto &cl : g.classes) {
+            ncoop += cl.coop > 0;
+            ntc += cl.coop == 2;
+        }
     out[8] = ncoop;
+    out[9] = ntc;
     if (reset) {
         ctx->hss_ms = ctx->hss_ms_sum = 0.0;
         ctx->hss_iters = ctx->launches = ctx->replays = 0;
@@ -1588,7 +1634,12 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
     for (int i = 0; i < (int)ctx->classes.size(); ++i)
         for (int r : ctx->classes[i].runs)
             if (r == 0) cls = i;
-    const RunClass &rc = ctx->classes[cls];
+    RunClass rc = ctx->classes[cls];
+    // the launch form the context chose for run 0 (held by its group's copy of the class)
+    for (auto &g : ctx->groups)
+        for (auto &gc : g.classes)
+            for (int r : gc.runs)
+                if (r == 0) rc = gc;
     // the single-pass form where the context uses it and all n walkers are resident
     int single = 0;
     if (ctx->rec.rec_len > 0) {
@@ -1608,7 +1659,10 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         CU(cudaMalloc(&R.x, sizeof(float) * rows * dp));
         CU(cudaMalloc(&rbase, sizeof(long)));
         CU(cudaMemcpyAsync(rbase, &zero_base, sizeof(long), cudaMemcpyHostToDevice, s));
-        CU(kind_launch(D.kind).hss1(D.tile, C, runs, 1, (int)n, R, rbase, rc.smem, rc.prec_in_smem, s));
+        if (rc.coop > 0)  // the context's dense form: 16 walkers per CTA sharing P (tensor cores if coop_tr = 0)
+            CU(kind_launch(D.kind).hss1_coop(D.tile, C, runs, 1, (int)n, R, rbase, rc.coop_smem, rc.coop_tr, s));
+        else
+            CU(kind_launch(D.kind).hss1(D.tile, C, runs, 1, (int)n, R, rbase, rc.smem, rc.prec_in_smem, s));
         CU(launch_hss_pick(C, runs, 1, (int)n, R, rbase, s));
     }
     for (int phase = 0; phase < 3; ++phase)

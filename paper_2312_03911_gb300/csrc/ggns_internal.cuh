@@ -85,8 +85,15 @@ struct RunDesc {
 // comp_a/comp_b: ISO kinds: a = 1/sigma^2, b = log w_k - d/2 log(2 pi sigma^2);
 //                dense kinds: a unused, b = log w_k - mu_k^T P mu_k / 2 (mixture).
 struct ParLayout {
-    long lo, hi, means, comp_a, comp_b, prec, pmu, total;
+    long lo, hi, means, comp_a, comp_b, prec, pmu, ptc, total;
 };
+// Dense kinds whose d_pad is 128, 256 or 512 also carry P pre-split into TF32 pairs and
+// laid out for the tensor cores (ggns_tc.cuh): d_pad/8 K-steps x (P_hi, P_lo) x d_pad/128
+// tiles of 128 rows x 8 columns in core-matrix order (2 d_pad^2 floats, global memory only).
+__host__ __device__ inline bool tc_layout(int kind, int d_pad)
+{
+    return (kind == NS_LIK_DENSE_GAUSS || kind == NS_LIK_DENSE_MIX) && d_pad % 128 == 0 && d_pad <= 512;
+}
 // Component slots of the parameter block: an isotropic mixture of up to 8
 // components is padded to 4 or 8 slots (a = 0, b = -inf, mean 0: weight exactly
 // 0), so its likelihood runs over a compile-time count.
@@ -117,6 +124,9 @@ __host__ __device__ inline ParLayout par_layout(int d, int d_pad, int n_comp, in
     if (kind == NS_LIK_DENSE_GAUSS || kind == NS_LIK_DENSE_MIX) o += (long)d * d_pad;
     L.pmu = o;
     if (kind == NS_LIK_DENSE_MIX) o += (long)n_comp * d_pad;
+    o = (o + 3) & ~3L;  // 16-byte aligned: the tensor-core layout is read by bulk copies
+    L.ptc = o;
+    if (tc_layout(kind, d_pad)) o += 2l * d_pad * d_pad;
     L.total = (o + 3) & ~3L;
     return L;
 }

@@ -65,10 +65,11 @@ struct KindLaunch {
     cudaError_t (*hss1)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                         const long *rec_base, size_t smem, int pis, cudaStream_t s);
     cudaError_t (*hss1_occ)(int tile, size_t smem, int *blocks_per_sm);
-    // CTA-cooperative single pass of the dense kinds (cudaErrorInvalidValue elsewhere)
+    // CTA-cooperative single pass of the dense kinds (cudaErrorInvalidValue elsewhere): tr > 0 rows
+    // of P per shared-memory tile with the contraction on CUDA cores; tr = 0 on the tensor cores
     cudaError_t (*hss1_coop)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                              const long *rec_base, size_t smem, int tr, cudaStream_t s);
-    cudaError_t (*hss1_coop_occ)(int tile, size_t smem, int *blocks_per_sm);
+    cudaError_t (*hss1_coop_occ)(int tile, size_t smem, int tr, int *blocks_per_sm);
 };
 const KindLaunch &kind_launch(int kind);
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ggns_internal.cuh"
+#include "ggns_tc.cuh"
 
 namespace ggns {
 
@@ -12,6 +13,7 @@ constexpr int HSS_THREADS = 128;
 // Shared-memory view of a run's likelihood parameters.
 struct ParView {
     const float *lo, *hi, *means, *a, *b, *prec, *pmu;
+    const float *ptc;  // P for the tensor cores (global memory; dense kinds with d_pad 128, 256, 512)
 };
 
 // Periodic prior (TORUS): wrap each real component of x into [lo, hi) after a move,
@@ -87,7 +89,7 @@ __device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *
     } else {
         v.prec = gp + L.prec;
     }
-    const long n_pmu = L.total - L.pmu;
+    const long n_pmu = L.ptc - L.pmu;
     if (n_pmu > 0) {
         for (long i = threadIdx.x; i < n_pmu; i += blockDim.x) sm[o + i] = gp[L.pmu + i];
         v.pmu = sm + o;
@@ -95,6 +97,7 @@ __device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *
     } else {
         v.pmu = nullptr;
     }
+    v.ptc = (L.total > L.ptc) ? gp + L.ptc : nullptr;
     return v;
 }
 
@@ -102,7 +105,7 @@ __device__ inline ParView load_params(const DevCtx &C, const RunDesc &D, float *
 __host__ __device__ inline long param_smem_floats(const RunDesc &D, bool prec_in_smem)
 {
     const ParLayout L = par_layout(D.d, D.d_pad, D.n_comp, D.kind);
-    long n = L.prec + (L.total - L.pmu);
+    long n = L.prec + (L.ptc - L.pmu);
     if (prec_in_smem) n += L.pmu - L.prec;
     return n;
 }
@@ -497,6 +500,23 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
     return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
 }
 
+// Dense likelihood of the 16 walkers of a CTA with the contraction on the tensor cores
+// (ggns_tc.cuh); every thread of the CTA calls it.  `ok` turns false if a wait gave up.
+template <int KIND, int E>
+__device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
+                              tc::State &T, bool &ok)
+{
+    const bool mix = (KIND == NS_LIK_DENSE_MIX);
+    float v[E], y[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int c = c0 + e;
+        v[e] = (c < D.d) ? (mix ? x[e] : x[e] - P.means[c]) : 0.f;
+    }
+    ok = tc::contract<E>(T, v, c0, D.d_pad, y);
+    return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
+}
+
 // ------------------------------------------------------------------------
 // Prior draws (Algorithm 3, first step): x ~ U(box) from Philox purpose 0.
 // One walker-tile group per point.
@@ -827,11 +847,13 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 // per refill.
 constexpr int COOP_THREADS = 512;
 
-template <int KIND, int G, int E, bool COOP = false>
+// TC (with COOP): the contraction of the cooperative walk on the tensor cores.
+template <int KIND, int G, int E, bool COOP = false, bool TC = false>
 __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : ((E >= 16) ? 2 : 4))
     k_hss1(DevCtx C, const int *run_list, RecView R, const long *rec_base, int prec_in_smem, int coop_tr)
 {
     static_assert(!COOP || G == 32, "one walker per warp");
+    static_assert(!TC || (COOP && COOP_THREADS == 32 * tc::WALKERS), "the tensor-core walk is the 16-warp CTA form");
     extern __shared__ float smem[];
     const int r = run_list[blockIdx.y];
     const RunDesc D = C.desc[r];
@@ -862,6 +884,16 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     bool coop_first = true;
     (void)coop_first;
     (void)coop_tr;
+    __shared__ int s_tc_fail;
+    tc::State T;
+    bool tc_ok = true;
+    if constexpr (TC) {
+        // a CTA without walkers of this run leaves before it takes tensor memory
+        if (static_cast<long>(blockIdx.x) * (blockDim.x / 32) >= W) return;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(rbase);
+        tc::setup(T, reinterpret_cast<char *>((a + 1023) & ~uintptr_t(1023)), P.ptc, dp, &s_tc_fail);
+    }
+    (void)tc_ok;
     const uint32_t iter = static_cast<uint32_t>(S->iter);
     const float dt = static_cast<float>(S->dt);
     const float lstar = static_cast<float>(S->lstar);
@@ -962,6 +994,12 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         }
         if constexpr (COOP) {
             if (!__syncthreads_or(active)) break;
+            if constexpr (TC) {
+                if (s_tc_fail) {
+                    if (threadIdx.x == 0) S->status = NS_ERR_TIMEOUT;
+                    break;
+                }
+            }
         } else {
             if (!__any_sync(0xffffffffu, active || !exhausted)) break;
         }
@@ -990,7 +1028,9 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         wrap_periodic<KIND, E>(D, P, x, c0);
         fold_box<KIND, E>(D, P, x, p, c0);
         float ll;
-        if constexpr (COOP) {
+        if constexpr (TC) {
+            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_ok);
+        } else if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
         } else {
             ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
@@ -1086,6 +1126,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             t = ts;
         }
     }
+    if constexpr (TC) tc::teardown(T);
 }
 
 // ------------------------------------------------------------------------

@@ -145,12 +145,39 @@ static cudaError_t coop_occ_t(size_t smem, int *blocks_per_sm)
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, 32, E, true>, COOP_THREADS, smem);
 }
+// The same CTA form with the contraction on the tensor cores (tr = 1).
+template <int E>
+static cudaError_t tc_t(const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R, const long *rec_base,
+                        size_t smem, cudaStream_t s)
+{
+    const int wpc = COOP_THREADS / 32;
+    const int bx = (max_k + wpc - 1) / wpc;
+    k_hss1<KIND, 32, E, true, true><<<dim3(bx, nr), COOP_THREADS, smem, s>>>(C, runs, R, rec_base, 0, 0);
+    return cudaGetLastError();
+}
+template <int E>
+static cudaError_t tc_occ_t(size_t smem, int *blocks_per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_hss1<KIND, 32, E, true, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, 32, E, true, true>, COOP_THREADS,
+                                                         smem);
+}
 template <int KD>
-static cudaError_t coop_dispatch(int tile, bool occ, const DevCtx *C, const int *runs, int nr, int max_k,
+static cudaError_t coop_dispatch(int tile, bool occ, bool tcore, const DevCtx *C, const int *runs, int nr, int max_k,
                                  const RecView *R, const long *rec_base, size_t smem, int tr, int *blocks_per_sm,
                                  cudaStream_t s)
 {
     if constexpr (KD == NS_LIK_DENSE_GAUSS || KD == NS_LIK_DENSE_MIX) {
+        if (tcore) {
+            switch (tile) {
+            case 6: return occ ? tc_occ_t<4>(smem, blocks_per_sm) : tc_t<4>(*C, runs, nr, max_k, *R, rec_base, smem, s);
+            case 7: return occ ? tc_occ_t<8>(smem, blocks_per_sm) : tc_t<8>(*C, runs, nr, max_k, *R, rec_base, smem, s);
+            case 8: return occ ? tc_occ_t<16>(smem, blocks_per_sm) : tc_t<16>(*C, runs, nr, max_k, *R, rec_base, smem, s);
+            default: return cudaErrorInvalidValue;
+            }
+        }
         switch (tile) {
         case 6: return occ ? coop_occ_t<4>(smem, blocks_per_sm) : coop_t<4>(*C, runs, nr, max_k, *R, rec_base, smem, tr, s);
         case 7: return occ ? coop_occ_t<8>(smem, blocks_per_sm) : coop_t<8>(*C, runs, nr, max_k, *R, rec_base, smem, tr, s);
@@ -164,11 +191,12 @@ static cudaError_t coop_dispatch(int tile, bool occ, const DevCtx *C, const int 
 static cudaError_t hss1_coop(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                              const long *rec_base, size_t smem, int tr, cudaStream_t s)
 {
-    return coop_dispatch<KIND>(tile, false, &C, runs, nr, max_k, &R, rec_base, smem, tr, nullptr, s);
+    return coop_dispatch<KIND>(tile, false, tr == 0, &C, runs, nr, max_k, &R, rec_base, smem, tr, nullptr, s);
 }
-static cudaError_t hss1_coop_occ(int tile, size_t smem, int *blocks_per_sm)
+static cudaError_t hss1_coop_occ(int tile, size_t smem, int tr, int *blocks_per_sm)
 {
-    return coop_dispatch<KIND>(tile, true, nullptr, nullptr, 0, 0, nullptr, nullptr, smem, 0, blocks_per_sm, nullptr);
+    return coop_dispatch<KIND>(tile, true, tr == 0, nullptr, nullptr, 0, 0, nullptr, nullptr, smem, tr, blocks_per_sm,
+                               nullptr);
 }
 
 }  // namespace GGNS_KIND_NS

@@ -231,11 +231,11 @@ class Sampler:
         _check(load().ns_restart(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF), self.h)
 
     def profile(self, reset: bool = False) -> dict:
-        out = (C.c_double * 9)()
+        out = (C.c_double * 10)()
         _check(load().ns_profile(self.h, out, int(reset)), self.h)
         return dict(hss_ms=out[0], hss_iters=int(out[1]), launches=int(out[2]), replays=int(out[3]),
                     hss_ms_sum=out[4], rec_overflows=int(out[5]), rec_len=int(out[6]), noise_steps=int(out[7]),
-                    coop_classes=int(out[8]))
+                    coop_classes=int(out[8]), tensor_classes=int(out[9]))
 
     def result(self, run: int = 0, check: bool = True) -> dict:
         r = Result()

@@ -580,18 +580,55 @@ def test_c1_posterior_moments_against_closed_form():
 
 def test_cooperative_dense_walk_equals_per_walker_walk():
     """d=256 dense mixture (P does not fit in shared memory): the walk in which the walkers of a
-    CTA share each tile of P gives the same runs, bit for bit, as one read of P per walker."""
+    CTA share each tile of P, with the contraction on CUDA cores (coop = 1), gives the same runs,
+    bit for bit, as one read of P per walker."""
     w = W.small_workload("dense_mix", 256, 160, seed=61)
     w = dict(w, cfg=dict(w["cfg"], n_steps=120, max_iters=12))
     out = {}
     for coop in (0, 1):
-        s = ggns.Sampler([dict(w, cfg=dict(w["cfg"], coop=0 if coop else -1))])
+        s = ggns.Sampler([dict(w, cfg=dict(w["cfg"], coop=1 if coop else -1))])
         s.step(12)
         out[coop] = (s.result(0, check=False), s.profile()["coop_classes"])
     assert out[0][1] == 0 and out[1][1] == 1
     a, b = out[0][0], out[1][0]
     for key in ("logz", "logz_err", "n_like", "dt", "n_iter", "n_dead"):
         assert a[key] == b[key], key
+
+
+@pytest.mark.parametrize("kind,d,n,steps", [("dense", 128, 32, 20), ("dense_mix", 256, 32, 12),
+                                            ("dense_mix", 512, 24, 10), ("dense", 512, 17, 12)])
+def test_tensor_core_dense_trajectories_match_oracle(kind, d, n, steps):
+    """The dense walk with the contraction y = P v on the tensor cores (tcgen05, 3xTF32, accumulators
+    in tensor memory): at most 20 steps from identical FP32 inputs give the same inside/outside
+    decisions, step counts and reservoir picks as the FP64 oracle, and outputs within 1e-5
+    (d_pad 128, 256, 512; a ragged last CTA of walkers)."""
+    w = W.small_workload(kind, d, 2 * n, seed=17)
+    w = dict(w, cfg=dict(w["cfg"], n_steps=steps))
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(6)
+    center = np.asarray(w["spec"]["means"])[0]
+    found = False
+    for attempt in range(20):
+        x0 = (center + _ball_start(d, n, 0.05, rng)).astype(np.float32).astype(np.float64)
+        l0 = np.array([lik.loglik(v) for v in x0])
+        lstar = float(np.float32(np.min(l0) - 1.0))
+        o = oracle.hss_batch(lik, w["lo"], w["hi"], oracle.make_cfg(**w["cfg"]), 3, x0, l0, lstar, 0.004, trace=True)
+        ll = o["trace"][:, :, 2 * d]
+        if np.min(np.abs(ll - lstar)) > 1e-5 * max(1.0, abs(lstar)) + 1e-3:
+            found = True
+            break
+    assert found
+    s = ggns.Sampler([w])
+    assert s.profile()["tensor_classes"] == 1
+    xo = torch.zeros((n, d), device="cuda")
+    lo_ = torch.zeros(n, device="cuda")
+    x0d, l0d = _dev(x0, torch.float32), _dev(l0, torch.float32)
+    st = s.hss(x0d.data_ptr(), l0d.data_ptr(), n, lstar, 0.004, 3, xo.data_ptr(), lo_.data_ptr())
+    assert o["n_out"] > 40  # the score (the reflection normal) is exercised
+    assert (st["t_save"], st["t_stop"]) == (o["t_save"], o["t_stop"])
+    assert (st["n_in"], st["n_out"]) == (o["n_in"], o["n_out"])
+    np.testing.assert_allclose(xo.cpu().numpy(), o["x"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(lo_.cpu().numpy(), o["logl"], rtol=1e-5, atol=1e-3)
 
 
 # ---------------------------------------------------------------- dense configurations at full size
