@@ -416,11 +416,12 @@ ns_status launch_term_join(ns_ctx *ctx, Group &g, cudaStream_t s)
     return NS_OK;
 }
 
-// The momentum noise of the next iteration, drawn ahead on the noise stream.
+// The momentum noise of the next iteration, drawn ahead on the noise stream (the
+// cooperative walks draw theirs where they use it).
 static ns_status launch_noise_ahead(ns_ctx *ctx, Group &g, int &n)
 {
     for (auto &cl : g.classes)
-        if (cl.single) {
+        if (cl.single && !cl.coop) {
             CU(launch_noise(ctx->dc, cl.runs_dev, (int)cl.runs.size(), NOISE_BLOCKS_PER_RUN, ctx->rec,
                             ctx->rec_base_dev, g.nz_stream));
             ++n;
@@ -440,7 +441,7 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
     const DevCtx &C = ctx->dc;
     int n = 0;
     bool any_single = false;
-    for (auto &cl : g.classes) any_single |= (cl.single != 0);
+    for (auto &cl : g.classes) any_single |= (cl.single != 0 && !cl.coop);
     const bool noise_ahead = any_single && ctx->rec.nT > 0;
     if (noise_ahead && first) {
         // fork: this iteration's momentum noise beside cluster finding and selection

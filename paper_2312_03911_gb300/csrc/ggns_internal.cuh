@@ -300,6 +300,72 @@ __device__ __forceinline__ float gmax(float v)
     return v;
 }
 
+// ------------------------------------------------------------------------
+// Lane rows in shared memory.  In the one-walker-per-warp kernels lane l holds the
+// E = d_pad / 32 consecutive components l E .. l E + E - 1, so a warp reading "its"
+// element e of a per-component vector hits addresses E floats apart: for E = 16
+// sixteen lanes share each bank.  A vector kept in shared memory for such a warp is
+// stored with the 16-byte quads of each lane row permuted: quad q of lane l sits at
+// quad q ^ qswz(l) of the row.  A quarter-warp (the eight lanes one 16-byte access
+// serves per pass) then reads quad q through eight distinct bank groups.
+// ------------------------------------------------------------------------
+template <int E>
+__host__ __device__ constexpr int qswz(int l)
+{
+    constexpr int m = E / 4;          // quads per lane row
+    constexpr int p2 = m & -m;        // largest power of two dividing m
+    constexpr int p = p2 > 8 ? 8 : p2;
+    if constexpr (E % 4 != 0 || p == 1) {
+        return 0;                     // odd quad counts reach eight bank groups unpermuted
+    } else if constexpr (p == 8) {
+        return l & 7;
+    } else {
+        return ((l * p) >> 3) & (p - 1);
+    }
+}
+
+// Stored position of component c of a lane-row-permuted vector.
+template <int E>
+__host__ __device__ constexpr int swz_col(int c)
+{
+    if constexpr (E % 4 != 0) {
+        return c;
+    } else {
+        const int l = c / E, w = c - l * E;
+        return l * E + (((w >> 2) ^ qswz<E>(l)) << 2) + (w & 3);
+    }
+}
+
+// Quad q (components lane E + 4 q .. + 3) of a lane-row-permuted vector `row`.
+template <int E>
+__device__ __forceinline__ float4 lane_quad(const float *row, int lane, int q)
+{
+    return reinterpret_cast<const float4 *>(row + lane * E)[q ^ qswz<E>(lane)];
+}
+
+// Permute `nrows` vectors of `len` floats (consecutive, 16-byte aligned, len a
+// multiple of 32 E) in shared memory into the lane-row layout.  Call by the whole
+// CTA; the caller synchronises afterwards.
+template <int E>
+__device__ inline void swizzle_rows(float *base, int nrows, int len)
+{
+    if constexpr (E % 4 == 0 && qswz<E>(1) + qswz<E>(2) + qswz<E>(4) != 0) {
+        const int qpr = len / 4;      // quads per vector
+        float4 *b4 = reinterpret_cast<float4 *>(base);
+        for (int i = threadIdx.x; i < nrows * qpr; i += blockDim.x) {
+            const int qi = i % qpr;
+            const int l = qi / (E / 4), q = qi - l * (E / 4);
+            const int q2 = q ^ qswz<E>(l % 32);
+            if (q2 > q) {
+                const int j = i - q + q2;
+                const float4 t = b4[i];
+                b4[i] = b4[j];
+                b4[j] = t;
+            }
+        }
+    }
+}
+
 // Order-preserving 32-bit key of a float; NaN maps to 0 (sorts first).
 __device__ __forceinline__ uint32_t float_key(float f)
 {

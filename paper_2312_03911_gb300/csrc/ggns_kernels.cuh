@@ -41,14 +41,15 @@ __device__ __forceinline__ void wrap_periodic(const RunDesc &D, const ParView &P
 // (the path unfolded on a line of period 2w folds into the box; an odd number of
 // crossings flips that momentum component), so the walker never leaves the prior
 // and the box takes no outside step.  Padded components (lo = hi = x = 0) never fold.
-template <int KIND, int E>
+// SWZ: lo and hi are in the lane-row layout (one-walker-per-warp kernels).
+template <int KIND, int E, bool SWZ = false>
 __device__ __forceinline__ void fold_box(const RunDesc &D, const ParView &P, float (&x)[E], float (&p)[E], int c0)
 {
     if constexpr (KIND != NS_LIK_TORUS) {
         if (!D.box_fold) return;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            const int c = c0 + e;
+            const int c = SWZ ? swz_col<E>(c0 + e) : c0 + e;
             const float lo = P.lo[c], hi = P.hi[c];
             if (!(x[e] < lo || x[e] > hi)) continue;
             const float w = hi - lo, w2 = 2.f * w;
@@ -166,54 +167,88 @@ __device__ __forceinline__ float lik_mix_slots(const ParView &P, int dp, const f
 }
 
 // Dense kinds after y = P v (v = x - mu, or x for the mixture): the quadratic
-// forms, the log-sum-exp over the components and the score.
-template <int KIND, int G, int E>
+// forms, the log-sum-exp over the components and the score.  SWZ: one walker per
+// warp (G = 32) with means and P mu in the lane-row layout, read as quads.
+template <int KIND, int G, int E, bool SWZ = false>
 __device__ __forceinline__ float dense_finish(const RunDesc &D, const ParView &P, const float (&x)[E],
                                               const float (&y)[E], float (&g)[E], int c0, float *dmu_w)
 {
+    static_assert(!SWZ || (G == 32 && E % 4 == 0), "lane rows of whole quads");
     const int dp = D.d_pad;
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
     const int K = mix ? D.n_comp : 1;
+    const int lane = threadIdx.x & 31;
     if (!mix) {
         float q = 0.f;
+        if constexpr (SWZ) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float r = x[e] - P.means[c0 + e];
-            q = fmaf(r, y[e], q);
-            g[e] = -y[e];
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 mu = lane_quad<E>(P.means, lane, h);
+                q = fmaf(x[4 * h] - mu.x, y[4 * h], q);
+                q = fmaf(x[4 * h + 1] - mu.y, y[4 * h + 1], q);
+                q = fmaf(x[4 * h + 2] - mu.z, y[4 * h + 2], q);
+                q = fmaf(x[4 * h + 3] - mu.w, y[4 * h + 3], q);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) q = fmaf(x[e] - P.means[c0 + e], y[e], q);
         }
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = -y[e];
         q = gsum<G>(q);
         if (dmu_w) dmu_w[0] = 1.f;
         return D.lik_const - 0.5f * q;
     }
+    // g accumulates the responsibility-weighted -(y - P mu_k), rescaled as the maximum moves
     float m = -INFINITY, s = 0.f;
-    float acc[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) acc[e] = 0.f;
+    for (int e = 0; e < E; ++e) g[e] = 0.f;
     for (int k = 0; k < K; ++k) {
-        const float *mu = P.means + (long)k * dp + c0;
-        const float *pm = P.pmu + (long)k * dp + c0;
+        const float *mu = P.means + (long)k * dp;
+        const float *pm = P.pmu + (long)k * dp;
         float q = 0.f;
+        if constexpr (SWZ) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) q = fmaf(x[e] - mu[e], y[e] - pm[e], q);
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 a = lane_quad<E>(mu, lane, h), b = lane_quad<E>(pm, lane, h);
+                q = fmaf(x[4 * h] - a.x, y[4 * h] - b.x, q);
+                q = fmaf(x[4 * h + 1] - a.y, y[4 * h + 1] - b.y, q);
+                q = fmaf(x[4 * h + 2] - a.z, y[4 * h + 2] - b.z, q);
+                q = fmaf(x[4 * h + 3] - a.w, y[4 * h + 3] - b.w, q);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) q = fmaf(x[e] - mu[c0 + e], y[e] - pm[c0 + e], q);
+        }
         q = gsum<G>(q);
         const float tk = P.b[k] - 0.5f * q;
         if (tk > m) {
             const float sc = (m == -INFINITY) ? 0.f : expf(m - tk);
             s *= sc;
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] *= sc;
+            for (int e = 0; e < E; ++e) g[e] *= sc;
             m = tk;
         }
         const float wk = expf(tk - m);
         s += wk;
+        if constexpr (SWZ) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = fmaf(-wk, y[e] - pm[e], acc[e]);
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 b = lane_quad<E>(pm, lane, h);
+                g[4 * h] = fmaf(-wk, y[4 * h] - b.x, g[4 * h]);
+                g[4 * h + 1] = fmaf(-wk, y[4 * h + 1] - b.y, g[4 * h + 1]);
+                g[4 * h + 2] = fmaf(-wk, y[4 * h + 2] - b.z, g[4 * h + 2]);
+                g[4 * h + 3] = fmaf(-wk, y[4 * h + 3] - b.w, g[4 * h + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = fmaf(-wk, y[e] - pm[c0 + e], g[e]);
+        }
         if (dmu_w) dmu_w[k] = tk;
     }
     const float inv = 1.f / s;
 #pragma unroll
-    for (int e = 0; e < E; ++e) g[e] = acc[e] * inv;
+    for (int e = 0; e < E; ++e) g[e] *= inv;
     if (dmu_w) {
         for (int k = 0; k < K; ++k) dmu_w[k] = expf(dmu_w[k] - m) * inv;
     }
@@ -437,15 +472,23 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
     // walkers 4 wg .. 4 wg + 3 by columns NC cg .. NC cg + NC - 1 (NC = d_pad / 128), so each
     // element of a P tile is read from shared memory by 4 threads instead of 16 warps.
     constexpr int NC = (E * 32) / 128;
-    static_assert(NC >= 1 && NC * 128 == E * 32, "d_pad a multiple of 128");
+    static_assert(NC >= 1 && NC <= 4 && NC * 128 == E * 32, "d_pad 128, 256 or 512");
     const int d = D.d, dp = D.d_pad;
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
+    // v to the walker's buffer (means in the lane-row layout; plain columns in rbuf)
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = c0 + e;
-        float v = 0.f;
-        if (c < d) v = mix ? x[e] : x[e] - P.means[c];
-        rbuf[c] = v;
+    for (int h = 0; h < E / 4; ++h) {
+        float4 v = make_float4(x[4 * h], x[4 * h + 1], x[4 * h + 2], x[4 * h + 3]);
+        if (!mix) {
+            const float4 mu = lane_quad<E>(P.means, threadIdx.x & 31, h);
+            v.x -= mu.x; v.y -= mu.y; v.z -= mu.z; v.w -= mu.w;
+        }
+        const int c = c0 + 4 * h;
+        if (c + 0 >= d) v.x = 0.f;
+        if (c + 1 >= d) v.y = 0.f;
+        if (c + 2 >= d) v.z = 0.f;
+        if (c + 3 >= d) v.w = 0.f;
+        reinterpret_cast<float4 *>(rbuf + c)[0] = v;
     }
     const int ntiles = (d + tr - 1) / tr;
     const int chunks_per_row = dp >> 2;
@@ -489,32 +532,72 @@ __device__ float lik_dense_coop(const RunDesc &D, const ParView &P, const float 
         }
         __syncthreads();  // the buffer of tile t is refilled by the load of tile t + 2
     }
-    // Y through the tile buffer (16 x d_pad floats fit in 2 tr d_pad), then each walker reads its columns
+    // Y through the tile buffer (16 x d_pad floats fit in 2 tr d_pad) in the lane-row
+    // layout (NC columns never straddle a quad), then each walker reads its quads
 #pragma unroll
-    for (int i = 0; i < 4; ++i) vec_store<NC>(ptile + (long)(4 * wg + i) * dp + NC * cg, acc[i]);
+    for (int i = 0; i < 4; ++i) vec_store<NC>(ptile + (long)(4 * wg + i) * dp + swz_col<E>(NC * cg), acc[i]);
     __syncthreads();
     float y[E];
-    const float *yrow = ptile + (long)(threadIdx.x >> 5) * dp + c0;
+    const float *yrow = ptile + (long)(threadIdx.x >> 5) * dp;
 #pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = yrow[e];
-    return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
+    for (int h = 0; h < E / 4; ++h) {
+        const float4 t = lane_quad<E>(yrow, threadIdx.x & 31, h);
+        y[4 * h] = t.x; y[4 * h + 1] = t.y; y[4 * h + 2] = t.z; y[4 * h + 3] = t.w;
+    }
+    return dense_finish<KIND, 32, E, true>(D, P, x, y, g, c0, nullptr);
+}
+
+// E consecutive floats of a lane (c0 a multiple of E, rows 16-byte aligned when E % 4 == 0):
+// float4 accesses where E allows, so a warp moves its rows in E/4 wide instructions.
+template <int E>
+__device__ __forceinline__ void row_load(const float *src, float (&v)[E])
+{
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q) {
+            const float4 t = reinterpret_cast<const float4 *>(src)[q];
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = src[e];
+    }
+}
+template <int E>
+__device__ __forceinline__ void row_store(float *dst, const float (&v)[E])
+{
+    if constexpr (E % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < E / 4; ++q)
+            reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) dst[e] = v[e];
+    }
 }
 
 // Dense likelihood of the 16 walkers of a CTA with the contraction on the tensor cores
 // (ggns_tc.cuh); every thread of the CTA calls it.  `ok` turns false if a wait gave up.
 template <int KIND, int E>
 __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
-                              tc::State &T, bool &ok)
+                              const tc::State &T, tc::Pipe &pp, bool &ok)
 {
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
-    float v[E], y[E];
+    // v is staged in g (the score is written only after the contraction)
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = c0 + e;
-        v[e] = (c < D.d) ? (mix ? x[e] : x[e] - P.means[c]) : 0.f;
+    for (int h = 0; h < E / 4; ++h) {
+        float4 mu = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!mix) mu = lane_quad<E>(P.means, threadIdx.x & 31, h);
+        const float m4[4] = {mu.x, mu.y, mu.z, mu.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = 4 * h + i;
+            g[e] = (c0 + e < D.d) ? x[e] - m4[i] : 0.f;
+        }
     }
-    ok = tc::contract<E>(T, v, c0, D.d_pad, y);
-    return dense_finish<KIND, 32, E>(D, P, x, y, g, c0, nullptr);
+    float y[E];
+    ok = tc::contract<E>(T, pp, g, D.d_pad, y);
+    return dense_finish<KIND, 32, E, true>(D, P, x, y, g, c0, nullptr);
 }
 
 // ------------------------------------------------------------------------
@@ -822,6 +905,37 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
     }
 }
 
+// The momentum noise of step `step` drawn (Philox) and applied four components at a
+// time, so that no array of normals stays live (E a multiple of 4); `add` false
+// draws only the first block.  Returns the step's reservoir word (the spare bits of
+// the lane's first block).  The same update as with the normals drawn ahead.
+template <int E>
+__device__ __forceinline__ uint32_t noise_in_place(const RunDesc &D, uint32_t iter, uint32_t slot, uint32_t step,
+                                                   int c0, bool add, float keep, float dlt, float (&p)[E])
+{
+    static_assert(E % 4 == 0, "whole Philox blocks");
+    uint32_t word = 0;
+#pragma unroll
+    for (int b = 0; b < E / 4; ++b) {
+        if (b > 0 && !add) break;
+        const U4 r = rng_block(D, iter, P_NOISE, slot, step, static_cast<uint32_t>((c0 >> 2) + b));
+        if (b == 0) word = spare_bits(r);
+        if (!add) break;
+        float z[4];
+        box_muller(r.x, r.y, z[0], z[1]);
+        box_muller(r.z, r.w, z[2], z[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = 4 * b + i;
+            if (D.noise_mode == 1)
+                p[e] = fmaf(keep, p[e], dlt * z[i] * ((c0 + e < D.d) ? 1.f : 0.f));
+            else
+                p[e] = p[e] * fmaf(dlt, z[i], 1.f);
+        }
+    }
+    return word;
+}
+
 // ------------------------------------------------------------------------
 // Single-pass HSS (Algorithm 5) when every walker of the launch is resident.
 // A walker steps, records each step (inside flag, reservoir word, log L and, for
@@ -856,12 +970,34 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     static_assert(!TC || (COOP && COOP_THREADS == 32 * tc::WALKERS), "the tensor-core walk is the 16-warp CTA form");
     extern __shared__ float smem[];
     const int r = run_list[blockIdx.y];
-    const RunDesc D = C.desc[r];
+    // the cooperative walk keeps the run's descriptor and parameter view in shared
+    // memory (read there when used) to leave its registers to the walker
+    __shared__ RunDesc sD;
+    __shared__ ParView sP;
+    RunDesc Dl;
+    if constexpr (COOP) {
+        if (threadIdx.x == 0) sD = C.desc[r];
+        __syncthreads();
+    } else {
+        Dl = C.desc[r];
+    }
+    const RunDesc &D = COOP ? sD : Dl;
     RunState *S = C.state + r;
     if (S->done) return;
-    const ParView P = load_params(C, D, smem, prec_in_smem);
+    const ParView Pl = load_params(C, D, smem, prec_in_smem);
+    if constexpr (COOP) {
+        if (threadIdx.x == 0) sP = Pl;
+    }
     float *rbase = smem + param_smem_floats(D, prec_in_smem);
     __syncthreads();
+    const ParView &P = COOP ? sP : Pl;
+    if constexpr (COOP) {
+        // the box, the means and P mu into the lane-row layout (read as quads below)
+        const ParLayout PL = par_layout(D.d, D.d_pad, D.n_comp, D.kind);
+        swizzle_rows<E>(smem + PL.lo, 2 + comp_slots(D.n_comp, D.kind), D.d_pad);
+        if (P.pmu) swizzle_rows<E>(const_cast<float *>(P.pmu), D.n_comp, D.d_pad);
+        __syncthreads();
+    }
     const long rb = rec_base[r];  // first record row of this run
     const int nsteps = (D.d_pad & 3) ? 0 : noise_steps(R.nT, S->t_stop_last);
     const long nrow0 = (rb / R.rec_len) * R.nT;  // first noise row of this run
@@ -885,7 +1021,8 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     (void)coop_first;
     (void)coop_tr;
     __shared__ int s_tc_fail;
-    tc::State T;
+    __shared__ tc::State T;
+    tc::Pipe tc_pipe;
     bool tc_ok = true;
     if constexpr (TC) {
         // a CTA without walkers of this run leaves before it takes tensor memory
@@ -902,9 +1039,11 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     volatile int *v_remain = &S->remain_max;
     volatile int *v_tstop = &S->t_stop1;
 
-    float x[E], p[E], g[E], eps[E], vmask[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) vmask[e] = (c0 + e < D.d) ? 1.f : 0.f;
+    // eps: the momentum noise of a step.  The cooperative walk draws it where it is
+    // used (Philox on the ALUs; nothing stays live across the step); the other walks
+    // load or draw it once the previous step is done, so that the load completes
+    // while the coming step runs.
+    float x[E], p[E], g[E], eps[E];
     int w = 0, t = 0, nref = 0, consec = 0;
     bool reg_min = false, reg_max = false;
     bool active = false, exhausted = false;
@@ -940,15 +1079,15 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
                 for (int e = 0; e < E; ++e) x[e] = src[e];
                 lane_normals<E>(D, iter, P_MOM, w, 0, c0, p);
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] *= vmask[e];
-                if (nsteps >= 1) {
-                    const long nr0 = nrow0 + (long)w * R.nT;
-                    const float *src = R.nz + nr0 * R.xs + c0;
-#pragma unroll
-                    for (int e = 0; e < E; ++e) eps[e] = src[e];
-                    spare = R.nsp[nr0];
-                } else {
-                    lane_normals<E>(D, iter, P_NOISE, w, 1, c0, eps, &spare);
+                for (int e = 0; e < E; ++e) p[e] = (c0 + e < D.d) ? p[e] : 0.f;
+                if constexpr (!COOP) {
+                    if (nsteps >= 1) {
+                        const long nr0 = nrow0 + (long)w * R.nT;
+                        row_load<E>(R.nz + nr0 * R.xs + c0, eps);
+                        spare = R.nsp[nr0];
+                    } else {
+                        lane_normals<E>(D, iter, P_NOISE, w, 1, c0, eps, &spare);
+                    }
                 }
                 t = nref = consec = 0;
                 rem_seen = 1;
@@ -1009,46 +1148,49 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
 
         // ---- one step of Algorithm 5 (as in k_hss)
         const int ts = t + 1;
-        const uint32_t res_word = __shfl_sync(0xffffffffu, spare, gbase);
-        float ecur[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) ecur[e] = eps[e];
-        if (ts + 1 <= nsteps) {
-            // drawn ahead; the load completes while this step runs
-            const long nr1 = nrow0 + (long)w * R.nT + ts;
-            const float *src = R.nz + nr1 * R.xs + c0;
-#pragma unroll
-            for (int e = 0; e < E; ++e) eps[e] = src[e];
-            spare = R.nsp[nr1];
-        } else {
-            lane_normals<E>(D, iter, P_NOISE, w, ts + 1, c0, eps, &spare);
-        }
+        uint32_t res_word = 0;
+        if constexpr (!COOP) res_word = __shfl_sync(0xffffffffu, spare, gbase);
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
-        fold_box<KIND, E>(D, P, x, p, c0);
+        fold_box<KIND, E, COOP>(D, P, x, p, c0);
         float ll;
         if constexpr (TC) {
-            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_ok);
+            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok);
         } else if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
         } else {
             ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
         }
-        int outbox = 0;
-        float nb[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int c = c0 + e;
-            nb[e] = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
-            outbox += (nb[e] != 0.f);
-        }
+        // the box normal n_e in {-1, 0, 1} (recomputed below for a reflection off the box);
         // the reflection's group sums are reduced together with the box count: four
         // independent trees instead of two in sequence behind a vote (same sums)
+        int outbox = 0;
         float pnb = 0.f, pg = 0.f, gg = 0.f;
+        if constexpr (COOP) {
+#pragma unroll
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 lo4 = lane_quad<E>(P.lo, lane, h), hi4 = lane_quad<E>(P.hi, lane, h);
+                const float lo[4] = {lo4.x, lo4.y, lo4.z, lo4.w}, hi[4] = {hi4.x, hi4.y, hi4.z, hi4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = 4 * h + i;
+                    const float nb = (x[e] < lo[i]) ? -1.f : ((x[e] > hi[i]) ? 1.f : 0.f);
+                    outbox += (nb != 0.f);
+                    pnb = fmaf(p[e], nb, pnb);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = c0 + e;
+                const float nb = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
+                outbox += (nb != 0.f);
+                pnb = fmaf(p[e], nb, pnb);
+            }
+        }
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-            pnb = fmaf(p[e], nb[e], pnb);
             pg = fmaf(p[e], g[e], pg);
             gg = fmaf(g[e], g[e], gg);
         }
@@ -1061,7 +1203,11 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             if (outbox > 0) {
                 const float cc = __fdividef(2.f * pnb, static_cast<float>(outbox));
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] = fmaf(-cc, nb[e], p[e]);
+                for (int e = 0; e < E; ++e) {
+                    const int c = COOP ? swz_col<E>(c0 + e) : c0 + e;
+                    const float nb = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
+                    p[e] = fmaf(-cc, nb, p[e]);
+                }
             } else if (gg > 0.f && gg <= 3.0e38f) {
                 const float cc = __fdividef(2.f * pg, gg);
 #pragma unroll
@@ -1073,22 +1219,33 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         }
         if (stepping) {
             // momentum noise (with noise_inside, an outside step only reflects)
-            if (!(outside && D.noise_inside)) {
+            if constexpr (COOP) {
+                // one walker per warp: `stepping` is uniform over the warp
+                spare = noise_in_place<E>(D, iter, w, ts, c0, !(outside && D.noise_inside), keep, dlt, p);
+                res_word = __shfl_sync(0xffffffffu, spare, 0);
+            } else if (!(outside && D.noise_inside)) {
                 if (D.noise_mode == 1) {
 #pragma unroll
-                    for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * ecur[e] * vmask[e]);
+                    for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * ((c0 + e < D.d) ? 1.f : 0.f));
                 } else {
 #pragma unroll
-                    for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, ecur[e], 1.f);
+                    for (int e = 0; e < E; ++e) p[e] = p[e] * fmaf(dlt, eps[e], 1.f);
+                }
+            }
+            // the next step's noise
+            if constexpr (!COOP) {
+                if (ts + 1 <= nsteps) {
+                    const long nr1 = nrow0 + (long)w * R.nT + ts;
+                    row_load<E>(R.nz + nr1 * R.xs + c0, eps);
+                    spare = R.nsp[nr1];
+                } else {
+                    lane_normals<E>(D, iter, P_NOISE, w, ts + 1, c0, eps, &spare);
                 }
             }
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;
             // record the step
-            if (!outside) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) rec_x[e] = x[e];
-            }
+            if (!outside) row_store<E>(rec_x, x);
             if (lig == 0) {
                 *rec_meta = make_uint2(res_word, outside ? 1u : 0u);
                 *rec_ll = ll;
@@ -1120,13 +1277,13 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
                 for (int e = 0; e < E; ++e) x[e] = src[e];
                 lane_normals<E>(D, iter, P_PRUNE, w, ts, c0, p);
 #pragma unroll
-                for (int e = 0; e < E; ++e) p[e] *= vmask[e];
+                for (int e = 0; e < E; ++e) p[e] = (c0 + e < D.d) ? p[e] : 0.f;
                 consec = 0;
             }
             t = ts;
         }
     }
-    if constexpr (TC) tc::teardown(T);
+    if constexpr (TC) tc::teardown(T, tc_pipe);
 }
 
 // ------------------------------------------------------------------------

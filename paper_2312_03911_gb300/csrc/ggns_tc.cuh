@@ -4,16 +4,22 @@
 // One CTA steps 16 walkers (one per warp).  Each step, the walkers' vectors v
 // (x - mu, or x for the mixture) are split into TF32 pairs v = v_hi + v_lo and
 // written to shared memory as the B operand (N = 16 walkers, K-major core
-// matrices).  The precision matrix, pre-split into P_hi + P_lo and pre-laid-out
-// in core-matrix order when the context is created, streams from global memory through a ring
-// of shared-memory stages (one K-step of 8 columns of P per stage, for every
-// 128-row M-tile) with 1-D bulk copies completing on mbarriers.  One thread
-// issues, per K-step and M-tile, the three MMAs of the 3xTF32 product
-// P_hi v_hi + P_hi v_lo + P_lo v_hi (M = 128, N = 16, K = 8, FP32 accumulation
-// in tensor memory), and refills each stage once its MMAs have completed.  The
-// accumulators, Y^T[d_pad][16] (P is symmetric, so Y^T = P V^T), are read back
-// with tcgen05.ld and handed to the walkers through shared memory.  The split
-// keeps the product at FP32 accuracy (the neglected P_lo v_lo is 2^-22 relative).
+// matrices).  The precision matrix, pre-split into P_hi + P_lo and pre-laid-out in
+// core-matrix order when the context is created, streams from global memory through
+// a ring of STAGES shared-memory stages of 32 KB (a stage holds P_hi and P_lo of one
+// K-step of 8 columns for every 128-row M-tile, or of several K-steps when d_pad is
+// small).  Lane 0 of warp 0 issues, per half, the MMAs of the 3xTF32 product
+// P_hi v_hi + P_hi v_lo + P_lo v_hi (M = 128, N = 16, K = 8, FP32 accumulation in
+// tensor memory: the three products in accumulators of their own, so that an MMA
+// never waits for the one issued just before it; they are added in the read-back)
+// and commits each stage's MMAs to that stage's `empty` barrier.
+// Stage s is refilled by lane 0 of warp 1 + s with a 1-D bulk copy once the MMAs
+// that read it are done: an SM completes the bulk copies of one issuing warp one
+// after another, so the copies of several warps are what keeps enough bytes in
+// flight to cover the latency of the L2.  The accumulators, Y^T[d_pad][16] (P is
+// symmetric, so Y^T = P V^T), are read back with tcgen05.ld and handed to the
+// walkers through shared memory.  The split keeps the product at FP32 accuracy
+// (the neglected P_lo v_lo is 2^-22 relative).
 //
 // Every wait is bounded (2 s): a wait that gives up sets the CTA's failure flag,
 // the run's status NS_ERR_TIMEOUT, and the kernel winds down, waiting (again
@@ -26,7 +32,8 @@ namespace ggns {
 namespace tc {
 
 constexpr int WALKERS = 16;                    // N of every MMA: one walker per warp of a 512-thread CTA
-constexpr int STAGES = 3;                      // shared-memory stages of P in flight
+constexpr int STAGES = 3;                      // shared-memory stages of P (one producer warp each)
+constexpr uint32_t STAGE_BYTES = 32768;        // bytes of one stage
 constexpr uint64_t WAIT_NS = 2000000000ull;    // a wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -116,14 +123,16 @@ __host__ __device__ constexpr uint32_t instr_desc_tf32(int M, int N)
            (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// (No memory clobber: the operands were published by the barriers and fences before
+// the MMAs; keeping shared-memory reads of the issuing loop in registers across the
+// MMAs is what lets one lane issue them back to back.)
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 // Arrive on `bar` once every MMA this thread issued so far has completed.
@@ -148,10 +157,19 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The B operand of K-step j (its 16 walkers x 8 columns, 512 bytes) starts at byte
+// vpos(j) of V_hi / V_lo.  A lane writes its E columns as quads into K-steps
+// lane E / 8 ..; one extra 16 bytes after every R = max(E / 8, 1) K-steps puts the
+// quads that the eight lanes of a quarter-warp write into distinct bank groups.
+__host__ __device__ constexpr int vgroup(int d_pad) { return d_pad >= 256 ? d_pad / 256 : 1; }
+__host__ __device__ constexpr uint32_t vpos(int j, int r) { return 512u * j + 16u * (j / r); }
+
 // Layout of the tensor-core state in dynamic shared memory (bytes from a 1024-aligned base).
 struct Plan {
-    int mt, ks;              // 128-row M-tiles and 8-column K-steps of d_pad
-    uint32_t stage_bytes;    // one K-step of P_hi and P_lo for every M-tile
+    int mt, ks, vr;          // 128-row M-tiles, 8-column K-steps of d_pad, K-steps per lane row
+    int units;               // halves (P_hi or P_lo of one K-step, mt x 4 KB) per stage
+    int npos;                // stages consumed by one contraction (2 ks / units)
+    uint32_t vbytes;         // one B operand (V_hi or V_lo)
     uint32_t v_off, stage_off, bar_off, total;
 };
 
@@ -160,10 +178,13 @@ __host__ __device__ inline Plan plan(int d_pad)
     Plan p;
     p.mt = d_pad / 128;
     p.ks = d_pad / 8;
-    p.stage_bytes = static_cast<uint32_t>(2 * p.mt * 4096);
-    p.v_off = 0;                                            // V_hi then V_lo: 2 x ks x 512 bytes
-    p.stage_off = p.v_off + static_cast<uint32_t>(2 * p.ks * 512);
-    p.bar_off = p.stage_off + STAGES * p.stage_bytes;       // full[S], empty[S], done, tmem base
+    p.vr = vgroup(d_pad);
+    p.units = static_cast<int>(STAGE_BYTES / (4096u * p.mt));
+    p.npos = 2 * p.ks / p.units;
+    p.vbytes = (vpos(p.ks, p.vr) + 127u) & ~127u;
+    p.v_off = 0;                                            // V_hi then V_lo
+    p.stage_off = p.v_off + 2 * p.vbytes;
+    p.bar_off = p.stage_off + STAGES * STAGE_BYTES;         // full[S], empty[S], done, tmem base
     p.total = p.bar_off + (2 * STAGES + 1) * 8 + 16;
     return p;
 }
@@ -171,43 +192,68 @@ __host__ __device__ inline Plan plan(int d_pad)
 // Floats of the pre-laid-out P of a run: ks K-steps x (P_hi, P_lo) x mt tiles x 1024.
 __host__ __device__ inline long ptc_floats(int d_pad) { return 2l * d_pad * d_pad; }
 
-// Per-CTA state (shared-memory pointers, tensor-memory base, pipeline counters).
+// Per-CTA state (shared-memory pointers, tensor-memory base), kept in shared memory:
+// thread 0 writes it, every thread reads it.
 struct State {
     float *vhi, *vlo;     // B operand (Y^T aliases vhi after the MMAs)
     char *stages;
     uint64_t *full, *empty, *done;
     uint32_t *tmem_slot;
     uint32_t tmem;        // tensor-memory base address (lane 0, first column)
-    uint32_t ncols;       // allocated columns
+    uint32_t ncols;       // allocated columns: accumulators hh, hl, lh of 16 columns per M-tile
     const float *ptc;     // pre-laid-out P of the run (global)
-    int mt, ks;
-    uint32_t stage_bytes;
-    long g;               // K-steps consumed so far (thread 0 only)
-    uint32_t done_phase;  // parity of the next completion of `done` (every thread)
+    int mt, ks, vr, units, npos;
     int *fail;            // shared failure flag
 };
 
-// CTA set-up: barriers, tensor memory, the first STAGES K-steps of P.  Every thread
-// calls it; `base` is 1024-byte aligned dynamic shared memory of plan(d_pad).total bytes.
+// Accumulator column of product k (0: P_hi v_hi, 1: P_hi v_lo, 2: P_lo v_hi) of M-tile m.
+__device__ __forceinline__ uint32_t acc_col(const State &T, int k, int m)
+{
+    return static_cast<uint32_t>((k * T.mt + m) * WALKERS);
+}
+
+// Each thread's view of the pipeline (32-bit counters, advanced incrementally): the
+// stage of the next contraction's first position and, for the thread that waits on
+// them, the parity of the next completion of the full barriers (MMA lane), of its
+// stage's empty barrier (producer lanes) and of `done` (every thread).
+struct Pipe {
+    int s0 = 0;
+    uint32_t full_par = 0, empty_par = 0, phase = 0;
+};
+
+__device__ __forceinline__ bool failed(const State &T) { return *reinterpret_cast<volatile int *>(T.fail) != 0; }
+
+// Halves idx * units .. of the contraction into stage s.
+__device__ __forceinline__ void fill(const State &T, int s, int idx)
+{
+    mbar_expect_tx(T.full + s, STAGE_BYTES);
+    bulk_copy(T.stages + (size_t)s * STAGE_BYTES, T.ptc + (size_t)idx * (STAGE_BYTES / 4), STAGE_BYTES, T.full + s);
+}
+
+// CTA set-up: barriers, tensor memory, the first STAGES stages of P.  Every thread
+// calls it; `T` is in shared memory; `base` is 1024-byte aligned dynamic shared memory
+// of plan(d_pad).total bytes.
 __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, int *fail_flag)
 {
-    const Plan pl = plan(d_pad);
-    T.vhi = reinterpret_cast<float *>(base + pl.v_off);
-    T.vlo = reinterpret_cast<float *>(base + pl.v_off + pl.ks * 512);
-    T.stages = base + pl.stage_off;
-    T.full = reinterpret_cast<uint64_t *>(base + pl.bar_off);
-    T.empty = T.full + STAGES;
-    T.done = T.empty + STAGES;
-    T.tmem_slot = reinterpret_cast<uint32_t *>(T.done + 1);
-    T.ptc = ptc;
-    T.mt = pl.mt;
-    T.ks = pl.ks;
-    T.stage_bytes = pl.stage_bytes;
-    T.g = 0;
-    T.done_phase = 0;
-    T.fail = fail_flag;
-    T.ncols = (pl.mt * WALKERS <= 32) ? 32u : static_cast<uint32_t>(pl.mt * WALKERS);  // a power of two
     if (threadIdx.x == 0) {
+        const Plan pl = plan(d_pad);
+        T.vhi = reinterpret_cast<float *>(base + pl.v_off);
+        T.vlo = reinterpret_cast<float *>(base + pl.v_off + pl.vbytes);
+        T.stages = base + pl.stage_off;
+        T.full = reinterpret_cast<uint64_t *>(base + pl.bar_off);
+        T.empty = T.full + STAGES;
+        T.done = T.empty + STAGES;
+        T.tmem_slot = reinterpret_cast<uint32_t *>(T.done + 1);
+        T.ptc = ptc;
+        T.mt = pl.mt;
+        T.ks = pl.ks;
+        T.vr = pl.vr;
+        T.units = pl.units;
+        T.npos = pl.npos;
+        T.fail = fail_flag;
+        uint32_t nc = 32;
+        while (nc < static_cast<uint32_t>(3 * pl.mt * WALKERS)) nc <<= 1;  // a power of two
+        T.ncols = nc;
         *fail_flag = 0;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(T.full + s, 1);
@@ -216,6 +262,7 @@ __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, 
         mbar_init(T.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(T.tmem_slot)),
                      "r"(T.ncols)
@@ -225,29 +272,29 @@ __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, 
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    T.tmem = *T.tmem_slot;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            const int j = s % T.ks;
-            mbar_expect_tx(T.full + s, T.stage_bytes);
-            bulk_copy(T.stages + (size_t)s * T.stage_bytes, T.ptc + (size_t)j * (T.stage_bytes / 4), T.stage_bytes,
-                      T.full + s);
-        }
+        T.tmem = *T.tmem_slot;
+        for (int s = 0; s < STAGES; ++s) fill(T, s, s % T.npos);
     }
+    __syncthreads();
 }
 
-// CTA wind-down: the copies still in flight (the prefetched stages) land, then the
-// tensor memory is freed.  Every thread calls it.
-__device__ inline void teardown(State &T)
+// CTA wind-down: the MMAs issued so far complete, the stages prefetched for a next
+// contraction land, then the tensor memory is freed.  Every thread calls it.
+__device__ inline void teardown(State &T, const Pipe &pp)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        // every MMA this thread issued has completed before the tensor memory is freed
         mma_commit(T.done);
-        if (!mbar_wait(T.done, T.done_phase)) *T.fail = 1;
+        if (!mbar_wait(T.done, pp.phase)) *T.fail = 1;
+        int s = pp.s0;
+        uint32_t par = pp.full_par;
         for (int i = 0; i < STAGES; ++i) {
-            const long g = T.g + i;
-            if (!mbar_wait(T.full + (g % STAGES), static_cast<uint32_t>((g / STAGES) & 1))) *T.fail = 1;
+            if (!mbar_wait(T.full + s, par)) *T.fail = 1;
+            if (++s == STAGES) {
+                s = 0;
+                par ^= 1u;
+            }
         }
     }
     fence_before_sync();
@@ -257,110 +304,154 @@ __device__ inline void teardown(State &T)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(T.tmem), "r"(T.ncols) : "memory");
 }
 
-// Thread 0: the MMAs of one contraction, refilling each stage of P once its MMAs are
-// done (the refill of the stage consumed by K-step j - 1 is issued after the MMAs of
-// K-step j, so the tensor pipe always has work queued while the thread waits).
-__device__ inline void issue(State &T)
+// Lane 0 of warp 0: the MMAs of one contraction (its npos stages, the first in stage
+// pp.s0) for d_pad = 128 MT.  The tile count is a compile-time constant so that the
+// MMAs of a stage form one straight sequence (one lane issues them back to back;
+// loop control between them slows the issue several-fold).  Within a half the
+// products are issued M-tile after M-tile, each into its own accumulator;
+// descriptors are built by adding shared-memory offsets (in 16-byte units) to the
+// descriptor of address 0.
+template <int MT>
+__device__ inline void issue_mmas(const State &T, Pipe &pp)
 {
+    constexpr int UNITS = static_cast<int>(STAGE_BYTES / (4096u * MT));  // halves per stage
+    constexpr int NPOS = 2 * (16 * MT) / UNITS;                            // stages per contraction
+    constexpr int VR = vgroup(128 * MT);
+    constexpr uint32_t ACC_HL = MT * WALKERS, ACC_LH = 2 * MT * WALKERS;
     const uint32_t idesc = instr_desc_tf32(128, WALKERS);
-    const uint32_t vhi = smem_addr(T.vhi), vlo = smem_addr(T.vlo), st0 = smem_addr(T.stages);
-    const uint32_t tile_bytes = 4096u, lo_off = static_cast<uint32_t>(T.mt) * 4096u;
-    const long g0 = T.g;
-    bool ok = true;
-    for (int j = 0; j < T.ks && ok; ++j) {
-        const long g = g0 + j;
-        const int s = static_cast<int>(g % STAGES);
-        if (!mbar_wait(T.full + s, static_cast<uint32_t>((g / STAGES) & 1))) {
-            ok = false;
-            break;
+    const uint32_t tmem = T.tmem;
+    uint64_t *const full = T.full, *const empty = T.empty;
+    const uint64_t d0 = smem_desc(0, 128, 256);
+    const uint32_t vhi = smem_addr(T.vhi) >> 4, vlo = smem_addr(T.vlo) >> 4, st0 = smem_addr(T.stages) >> 4;
+    int s = pp.s0;
+    uint32_t par = pp.full_par;
+#pragma unroll 1
+    for (int i = 0; i < NPOS; ++i) {
+        if (failed(T) || !mbar_wait(full + s, par)) {
+            *T.fail = 1;
+            return;
         }
         fence_after_sync();
-        const uint32_t sa = st0 + static_cast<uint32_t>(s) * T.stage_bytes;
-        const uint64_t bh = smem_desc(vhi + 512u * j, 128, 256), bl = smem_desc(vlo + 512u * j, 128, 256);
-        for (int m = 0; m < T.mt; ++m) {
-            const uint64_t ah = smem_desc(sa + m * tile_bytes, 128, 256);
-            const uint64_t al = smem_desc(sa + lo_off + m * tile_bytes, 128, 256);
-            const uint32_t d = T.tmem + static_cast<uint32_t>(m * WALKERS);
-            mma_tf32(d, ah, bh, idesc, j > 0 ? 1u : 0u);
-            mma_tf32(d, ah, bl, idesc, 1u);
-            mma_tf32(d, al, bh, idesc, 1u);
-        }
-        mma_commit(T.empty + s);
-        if (j >= 1) {
-            const long gp = g - 1;
-            const int sp = static_cast<int>(gp % STAGES);
-            if (!mbar_wait(T.empty + sp, static_cast<uint32_t>((gp / STAGES) & 1))) {
-                ok = false;
-                break;
+        const uint32_t sa = st0 + static_cast<uint32_t>(s) * (STAGE_BYTES >> 4);
+#pragma unroll
+        for (int u = 0; u < UNITS; ++u) {
+            const int q = i * UNITS + u;  // half: K-step q / 2, P_lo if q odd
+            const int j = q >> 1;
+            const uint32_t vj = vpos(j, VR) >> 4;
+            const uint32_t acc = j > 0 ? 1u : 0u;
+            const uint64_t bh = d0 + vhi + vj;
+            const uint64_t a0 = d0 + sa + static_cast<uint32_t>(u * MT) * 256u;
+            if ((u & 1) == 0) {  // UNITS is even: the parity of q is that of u
+                const uint64_t bl = d0 + vlo + vj;
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_tf32(tmem + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_tf32(tmem + ACC_HL + m * WALKERS, a0 + 256u * m, bl, idesc, acc);
+            } else {
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_tf32(tmem + ACC_LH + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
             }
-            const int jn = static_cast<int>((gp + STAGES) % T.ks);
-            mbar_expect_tx(T.full + sp, T.stage_bytes);
-            bulk_copy(T.stages + (size_t)sp * T.stage_bytes, T.ptc + (size_t)jn * (T.stage_bytes / 4),
-                      T.stage_bytes, T.full + sp);
+        }
+        mma_commit(empty + s);
+        if (++s == STAGES) {
+            s = 0;
+            par ^= 1u;
         }
     }
-    if (ok) {
-        const long gp = g0 + T.ks - 1;
-        const int sp = static_cast<int>(gp % STAGES);
-        if (mbar_wait(T.empty + sp, static_cast<uint32_t>((gp / STAGES) & 1))) {
-            const int jn = static_cast<int>((gp + STAGES) % T.ks);
-            mbar_expect_tx(T.full + sp, T.stage_bytes);
-            bulk_copy(T.stages + (size_t)sp * T.stage_bytes, T.ptc + (size_t)jn * (T.stage_bytes / 4),
-                      T.stage_bytes, T.full + sp);
-        } else {
-            ok = false;
-        }
-    }
-    if (!ok) {
-        *T.fail = 1;
-        return;
-    }
-    T.g = g0 + T.ks;
+    pp.full_par = par;
     mma_commit(T.done);
 }
 
-// y = P v for the 16 walkers of the CTA (lane l of warp n holds components c0 .. c0+E-1
-// of walker n).  Every thread of the CTA calls it (barriers inside).  Returns false if
-// a wait gave up (y is then undefined).
-template <int E>
-__device__ inline bool contract(State &T, const float (&v)[E], int c0, int d_pad, float (&y)[E])
+// Lane 0 of warp 1 + w: the refills of stage w during one contraction (positions
+// STAGES .. npos + STAGES - 1 of the contraction, counted from its first, that fall
+// in stage w; those past npos prefetch the next contraction), each once the MMAs
+// that read the stage's previous content are done.
+__device__ inline void refill_stage(const State &T, Pipe &pp, int w)
 {
+    int idx = STAGES + (w - pp.s0 + STAGES) % STAGES;
+    for (; idx < T.npos + STAGES; idx += STAGES) {
+        if (failed(T) || !mbar_wait(T.empty + w, pp.empty_par)) {
+            *T.fail = 1;
+            return;
+        }
+        pp.empty_par ^= 1u;
+        fill(T, w, idx < T.npos ? idx : idx - T.npos);
+    }
+}
+
+// y = P v for the 16 walkers of the CTA (lane l of warp n holds components l E ..
+// l E + E - 1 of walker n).  Every thread of the CTA calls it (barriers inside).
+// Returns false if a wait gave up (y is then undefined).
+template <int E>
+__device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], int d_pad, float (&y)[E])
+{
+    static_assert(E % 4 == 0, "quads of columns");
+    static_assert(STAGES + 1 <= WALKERS, "a producer warp per stage besides the issuing warp");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // B operand: element (walker n, column c) at K-step c / 8, core matrix ((n / 8), (c % 8) / 4)
+    // B operand: the quad (walker n, columns c .. c + 3) is row n % 8 of core matrix
+    // (c % 8) / 4 of walker group n / 8 in K-step c / 8
+    char *vh = reinterpret_cast<char *>(T.vhi), *vl = reinterpret_cast<char *>(T.vlo);
+    const uint32_t row_off = static_cast<uint32_t>((warp >> 3) * 256 + (warp & 7) * 16);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int c = c0 + e, j = c >> 3, kk = c & 7;
-        const int off = j * 128 + (warp >> 3) * 64 + (kk >> 2) * 32 + (warp & 7) * 4 + (kk & 3);  // floats
-        const uint32_t hi = to_tf32(v[e]);
-        const uint32_t lo = to_tf32(v[e] - __uint_as_float(hi));
-        T.vhi[off] = __uint_as_float(hi);
-        T.vlo[off] = __uint_as_float(lo);
+    for (int q = 0; q < E / 4; ++q) {
+        const int c = lane * E + 4 * q;
+        const uint32_t off = vpos(c >> 3, T.vr) + row_off + static_cast<uint32_t>(((c >> 2) & 1) * 128);
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t hi = to_tf32(v[4 * q + i]);
+            h[i] = __uint_as_float(hi);
+            l[i] = __uint_as_float(to_tf32(v[4 * q + i] - h[i]));
+        }
+        *reinterpret_cast<float4 *>(vh + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(vl + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
     fence_async_smem();
     __syncthreads();
-    if (threadIdx.x == 0 && !*T.fail) {
-        fence_after_sync();
-        issue(T);
+    if (warp <= STAGES) {
+        // the working lane's warp-mates wait at the warp barrier, not in a blocking
+        // mbarrier test that would hold the working lane's warp as well
+        if (lane == 0) {
+            if (warp == 0) {
+                fence_after_sync();
+                issue_mmas<E / 4>(T, pp);
+            } else {
+                refill_stage(T, pp, warp - 1);
+            }
+        }
+        __syncwarp();
     }
+    pp.s0 = (pp.s0 + T.npos) % STAGES;
     // every thread: the accumulators are complete
-    const bool ok = mbar_wait(T.done, T.done_phase);
-    T.done_phase ^= 1u;
+    const bool ok = !failed(T) && mbar_wait(T.done, pp.phase);
+    pp.phase ^= 1u;
     fence_after_sync();
-    float *ybuf = T.vhi;  // Y^T[walker][d_pad] over the B operand, free once the MMAs are done
+    // Y^T[walker][d_pad] over the B operand (free once the MMAs are done), each walker's
+    // row in the lane-row layout so that the walker reads it back in quads
+    float *ybuf = T.vhi;
     if (ok && warp < 4 * T.mt) {
         const int m = warp >> 2, q = warp & 3;
-        float acc[16];
-        tmem_load16(T.tmem + (static_cast<uint32_t>(32 * q) << 16) + static_cast<uint32_t>(m * WALKERS), acc);
-        const int row = m * 128 + 32 * q + lane;
+        const uint32_t lanes = static_cast<uint32_t>(32 * q) << 16;
+        float hh[16], hl[16], lh[16];
+        tmem_load16(T.tmem + lanes + acc_col(T, 0, m), hh);
+        tmem_load16(T.tmem + lanes + acc_col(T, 1, m), hl);
+        tmem_load16(T.tmem + lanes + acc_col(T, 2, m), lh);
+        const int row = swz_col<E>(m * 128 + 32 * q + lane);
 #pragma unroll
-        for (int n = 0; n < WALKERS; ++n) ybuf[n * d_pad + row] = acc[n];
+        for (int n = 0; n < WALKERS; ++n) ybuf[n * d_pad + row] = hh[n] + (hl[n] + lh[n]);
     }
     fence_before_sync();
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < E; ++e) y[e] = ybuf[warp * d_pad + c0 + e];
+    for (int q = 0; q < E / 4; ++q) {
+        const float4 t = lane_quad<E>(ybuf + warp * d_pad, lane, q);
+        y[4 * q] = t.x;
+        y[4 * q + 1] = t.y;
+        y[4 * q + 2] = t.z;
+        y[4 * q + 3] = t.w;
+    }
     __syncthreads();  // ybuf is the next contraction's B operand
-    return ok && !*T.fail;
+    return ok && !failed(T);
 }
 
 }  // namespace tc
