@@ -117,6 +117,9 @@ typedef struct {
                           1: the box reflects a walker exactly (its position folds back across the
                           face, that momentum component flips; no outside step), so only the
                           iso-likelihood boundary of Algorithm 5 counts as outside              */
+    int fold_counts;   /* with box_fold 1: 1 counts an inside step on which the box reflected the
+                          walker as a reflection for the adaptive step size (Section 3: dt follows
+                          the number of reflections); it never counts toward n_ref or the pick  */
     /* Launch choices; 0 selects the library's own choice.  Options marked (context) are read
      * from the first configuration of a batch; tile from the first run of each (kind, d).    */
     int tile;          /* walker tile id + 1: 1..N_TILES (G lanes x E components, ns_tile_shape) */
@@ -133,7 +136,7 @@ typedef struct {
  * delta_p 0.5, tol 0.01, min_ref 1, max_ref 3, prune_after 10, termination 0,
  * clustering 1, noise_mode 1, out_lo 0.05, out_hi 0.15, seed 0, run_id 0,
  * max_iters 100000, dead_cap 0, noise_inside 1, pick_all 1, territory 1,
- * keep_last 0, box_fold 0 and every launch choice 0 (the library's own). */
+ * keep_last 0, box_fold 0, fold_counts 0 and every launch choice 0 (the library's own). */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context for one run.  Copies the box, the likelihood parameters and
@@ -267,8 +270,10 @@ ns_status ns_lik_backward(const ns_ctx *ctx, const float *x_dev, long n, const f
 /* Algorithm 5 on caller data for run 0 of ctx: n walkers start at x0_dev[n][d]
  * (FP32, all inside L > lstar) with step dt at iteration `iter`; walker j uses
  * Philox slot j.  Writes the new points x_out_dev[n][d], logl_out_dev[n], the
- * per-walker step counts steps_dev[n] (may be NULL) and, in stats_host[4],
- * (n_in, n_out, t_save, t_stop). */
+ * per-walker step counts steps_dev[n] (may be NULL) and, in stats_host[5],
+ * (n_in, n_out, t_save, t_stop, n_fold): inside and outside steps, the first
+ * saving step, the last step, and the inside steps on which the box reflected a
+ * walker (box_fold). */
 ns_status ns_hss(const ns_ctx *ctx, const float *x0_dev, const float *logl0_dev, long n, float lstar,
                  double dt, uint32_t iter, float *x_out_dev, float *logl_out_dev, int *steps_dev,
                  long *stats_host, void *stream);

@@ -56,12 +56,12 @@ class CfgT(C.Structure):
                 ("max_iters", C.c_int), ("noise_mode", C.c_int),
                 ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int), ("keep_last", C.c_int),
                 ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int),
-                ("box_fold", C.c_int)]
+                ("box_fold", C.c_int), ("fold_counts", C.c_int)]
 
 
 class BatchStatsT(C.Structure):
     _fields_ = [("n_in", C.c_long), ("n_out", C.c_long), ("t_save", C.c_int), ("t_stop", C.c_int),
-                ("n_fallback", C.c_int)]
+                ("n_fallback", C.c_int), ("n_fold", C.c_long)]
 
 
 class ResultT(C.Structure):
@@ -180,7 +180,8 @@ class Likelihood:
 def make_cfg(**kw) -> CfgT:
     c = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.05, tol=0.01, min_ref=1, max_ref=3,
              prune_after=10, termination=0, clustering=0, seed=0, run_id=0, max_iters=100000,
-             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0, noise_inside=0, pick_all=0, territory=0, box_fold=0)
+             noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0, noise_inside=0, pick_all=0, territory=0, box_fold=0,
+             fold_counts=0)
     c.update(kw)
     return CfgT(**c)
 
@@ -216,7 +217,7 @@ def hss_batch(lik: Likelihood, lo, hi, cfg: CfgT, it, x0, logl0, lstar, dt, trac
                         _dp(x0), _dp(logl0), float(lstar), float(dt), _dp(xo), _dp(lo_out), _ip(steps),
                         C.byref(st), _dp(tr))
     out = dict(x=xo, logl=lo_out, n_in=st.n_in, n_out=st.n_out, t_save=st.t_save, t_stop=st.t_stop,
-               n_fallback=st.n_fallback)
+               n_fallback=st.n_fallback, n_fold=st.n_fold)
     if trace:
         out["trace"] = tr[: st.t_stop]
     return out

@@ -338,12 +338,15 @@ typedef struct {
     int box_fold;     /* 1: the prior box reflects a walker exactly (the position folds back across
                          the face and the momentum component flips; not an outside step); 0: leaving
                          the box is an outside step that reflects off the violated faces */
+    int fold_counts;  /* with box_fold: an inside step on which the box reflected the walker counts
+                         as a reflection for the step-size control (not for n_ref or the pick) */
 } orc_cfg_t;
 
 typedef struct {
     long n_in, n_out;     /* inside / outside steps over all walkers          */
     int t_save, t_stop;   /* first saving step, last step taken               */
     int n_fallback;       /* walkers that saved nothing and return their start */
+    long n_fold;          /* inside steps on which the box reflected the walker (box_fold) */
 } orc_batch_stats_t;
 
 /*
@@ -391,7 +394,7 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
     int *count = (int *)calloc(n, sizeof(int));
     int *outside = (int *)calloc(n, sizeof(int));
     double *logl_now = (double *)malloc(sizeof(double) * n);
-    long n_in = 0, n_out = 0;
+    long n_in = 0, n_out = 0, n_fold = 0;
     int t_save = 0, t = 0, saving = 0;
     memcpy(x, x0, sizeof(double) * nd);
     for (int j = 0; j < n; ++j)
@@ -415,11 +418,13 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
                     if (u < 0.0) u += w;
                     xj[i] = lo[i] + u;
                 }
-            else if (cfg->box_fold)
+            int folded = 0;
+            if (!cfg->periodic && cfg->box_fold)
                 for (int i = 0; i < d; ++i) {
                     /* specular reflection off the faces lo_i, hi_i: the path unfolded on a
                      * line of period 2w folds back; an odd number of crossings flips p_i */
                     if (xj[i] >= lo[i] && xj[i] <= hi[i]) continue;
+                    folded = 1;
                     const double w = hi[i] - lo[i];
                     double u = fmod(xj[i] - lo[i], 2.0 * w);
                     if (u < 0.0) u += 2.0 * w;
@@ -477,7 +482,7 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
             n_ref[j] += out;
             outside[j] = out;
             logl_now[j] = logl;
-            if (out) { ++n_out; ++consec[j]; } else { ++n_in; consec[j] = 0; }
+            if (out) { ++n_out; ++consec[j]; } else { ++n_in; consec[j] = 0; n_fold += folded; }
         }
         /* trajectory preservation: save inside states once every walker has
          * reflected at least min_ref times */
@@ -527,7 +532,10 @@ int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const d
         }
         if (steps_out) steps_out[j] = t;
     }
-    if (st) { st->n_in = n_in; st->n_out = n_out; st->t_save = t_save; st->t_stop = t; st->n_fallback = n_fb; }
+    if (st) {
+        st->n_in = n_in; st->n_out = n_out; st->t_save = t_save; st->t_stop = t; st->n_fallback = n_fb;
+        st->n_fold = n_fold;
+    }
     free(x); free(p); free(xr); free(lr); free(g); free(nrm); free(eps);
     free(n_ref); free(consec); free(count); free(outside); free(logl_now);
     return 0;
@@ -1053,7 +1061,7 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
             new_label[j] = chosen;
         }
         /* --- HSS for every new point (Algorithm 5) --- */
-        long sum_in = 0, sum_out = 0;
+        long sum_in = 0, sum_out = 0, sum_fold = 0;
         {
             double *xs0 = xf_start;
             double *ls0 = lf_start;
@@ -1063,7 +1071,7 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
             }
             orc_batch_stats_t bs;
             orc_hss_batch(lk, logdetP, lo, hi, cfg, (uint32_t)it, k, xs0, ls0, lstar, dt, xnew, lnew, NULL, &bs, NULL);
-            sum_in = bs.n_in; sum_out = bs.n_out;
+            sum_in = bs.n_in; sum_out = bs.n_out; sum_fold = bs.n_fold;
             n_like += (long)k * bs.t_stop; n_steps_total += (long)k * bs.t_stop;
             n_fallback += bs.n_fallback;
         }
@@ -1091,7 +1099,9 @@ int orc_run(const orc_cfg_t *cfg, const double *lo, const double *hi, const orc_
             }
         }
         /* --- step-size adaptation from out_frac --- */
-        double out_frac = (sum_in + sum_out) > 0 ? (double)sum_out / (double)(sum_in + sum_out) : 0.0;
+        /* (with box_fold and fold_counts, the box's exact reflections count as reflections) */
+        const long n_refl = sum_out + ((cfg->box_fold && cfg->fold_counts) ? sum_fold : 0);
+        double out_frac = (sum_in + sum_out) > 0 ? (double)n_refl / (double)(sum_in + sum_out) : 0.0;
         if (out_frac > cfg->out_hi) dt *= 0.9;
         else if (out_frac < cfg->out_lo) dt *= 1.1;
         /* --- insert the new points: walker j fills the j-th killed slot --- */

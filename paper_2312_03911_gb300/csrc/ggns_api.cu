@@ -619,6 +619,7 @@ void ns_config_default(ns_config *c)
     c->pick_all = 1;
     c->territory = 1;
     c->box_fold = 0;
+    c->fold_counts = 0;
 }
 
 const char *ns_last_error(const ns_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -666,6 +667,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.territory = c.territory ? 1 : 0;
         D.keep_last = c.keep_last ? 1 : 0;
         D.box_fold = c.box_fold ? 1 : 0;
+        D.fold_counts = c.fold_counts ? 1 : 0;
         D.delta_p = (float)c.delta_p;
         D.keep = (float)std::sqrt(std::max(0.0, 1.0 - c.delta_p * c.delta_p));
         D.rosen_scale = (float)lik[r].rosen_scale;
@@ -732,8 +734,8 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         CU(cudaMalloc(&ctx->lastkey, sizeof(unsigned long long) * pt));
         CU(cudaMalloc(&ctx->start_slot, sizeof(int) * w));
         CU(cudaMalloc(&ctx->new_label, sizeof(int) * w));
-        CU(cudaMalloc(&ctx->wint, sizeof(int) * w * 8));
-        CU(cudaMemset(ctx->wint, 0, sizeof(int) * w * 8));
+        CU(cudaMalloc(&ctx->wint, sizeof(int) * w * WINT));
+        CU(cudaMemset(ctx->wint, 0, sizeof(int) * w * WINT));
         CU(cudaMalloc(&ctx->wres, sizeof(float) * w));
         for (int r = 0; r < n_runs; ++r)
             CU(cudaMemcpy(ctx->fa + ctx->desc[r].par_off, pars[r].data(), sizeof(float) * pars[r].size(),
@@ -1578,7 +1580,7 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
     CU(cudaMalloc(&order, sizeof(int) * 2 * n));
     CU(cudaMalloc(&start, sizeof(int) * n));
     CU(cudaMalloc(&nlab, sizeof(int) * n));
-    CU(cudaMalloc(&wint, sizeof(int) * 8 * n));
+    CU(cudaMalloc(&wint, sizeof(int) * WINT * n));
     CU(cudaMalloc(&wres, sizeof(float) * n));
     CU(cudaMalloc(&dx, sizeof(float) * n * dp));
     CU(cudaMalloc(&dl, sizeof(float) * n));
@@ -1683,6 +1685,7 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         stats_host[1] = S.n_out;
         stats_host[2] = S.t_save;
         stats_host[3] = S.t_stop;
+        stats_host[4] = S.n_fold;
     }
     return NS_OK;
 }

@@ -14,6 +14,7 @@ constexpr int KNN_K = 16;       // neighbour ranks precomputed per point for Alg
 constexpr int NLIVE_MAX = 16384;
 constexpr int KMAX_COMP = 64;   // mixture components
 constexpr int DMAX = 512;
+constexpr int WINT = 16;        // ints of walker state per walker (three-phase HSS)
 
 // Philox counter purposes (the fourth counter word is (iteration << 4) | purpose).
 enum Purpose : uint32_t {
@@ -56,7 +57,8 @@ struct RunDesc {
     int d, d_pad, n_live, k, kind, n_comp;
     int n_steps, min_steps, min_ref, max_ref, prune_after, termination, clustering, noise_mode;
     int noise_inside, pick_all, territory, keep_last;  // readings of Algorithm 5 (ns_config)
-    int box_fold, pad2_;                               // exact reflection off the prior box
+    int box_fold, fold_counts;                         // exact reflection off the prior box; its
+                                                       // reflections in the step-size control
     float delta_p, keep, rosen_scale, lik_const;
     float torus_a, torus_b, torus_c;  // TORUS: sine and cosine frequencies, offset
     double log_tol, out_lo, out_hi, dt_init;
@@ -154,6 +156,7 @@ struct RunState {
     int n_rec_overflow;    // iterations redone in three phases
     int kill_cnt[CMAX];    // kills per cluster in the current iteration
     int spawn_cnt[CMAX];   // new points per cluster in the current iteration
+    long n_fold;           // inside steps on which the box reflected the walker (box_fold)
 };
 
 // FP64 cluster statistics of one run (Appendix H), log space.
@@ -176,7 +179,7 @@ struct DevCtx {
     int *order;       // [sum n_live]  ascending (logL, slot) order of the last selection
     int *start_slot;  // [sum k]
     int *new_label;   // [sum k]
-    int *wint;        // [sum k][8]     walker integer state
+    int *wint;        // [sum k][WINT]  walker integer state
     float *wres_logl; // [sum k]
     int *nbr;         // [sum n_live][KNN_K]
 };

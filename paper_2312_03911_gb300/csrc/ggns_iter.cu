@@ -704,6 +704,7 @@ __device__ void sort_body(DevCtx C, int r, unsigned char *sraw)
         S->t_stop = 0;
         S->n_in = 0;
         S->n_out = 0;
+        S->n_fold = 0;
         S->wcount1 = 0;
         S->t_save1 = 0;
         S->t_stop1 = 0;
@@ -819,8 +820,10 @@ __global__ void k_tail(DevCtx C, int r0)
     __syncthreads();
     if (threadIdx.x != 0) return;
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_max[w]);
+    // the reflections per step (with box_fold and fold_counts, the box's exact reflections count)
     const long tot = S->n_in + S->n_out;
-    const double out_frac = tot > 0 ? (double)S->n_out / (double)tot : 0.0;
+    const long nrefl = S->n_out + ((D.box_fold && D.fold_counts) ? S->n_fold : 0);
+    const double out_frac = tot > 0 ? (double)nrefl / (double)tot : 0.0;
     if (out_frac > D.out_hi) S->dt *= 0.9;
     else if (out_frac < D.out_lo) S->dt *= 1.1;
     S->n_like += (long)D.k * S->t_stop;
@@ -896,20 +899,21 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
     const long base = rec_base[r] + (long)w * R.rec_len;
     // the steps of the window that enter the reservoir: inside steps from t_save on;
     // with pick_all every step, a drawn outside step rejecting (the start point)
-    int pick = 0, count = 0, nout = 0;
+    int pick = 0, count = 0, nout = 0, nfold = 0;
     bool pick_out = false;
     for (int t0 = 1; t0 <= tstop; t0 += 32) {
         const int t = t0 + lane;
         uint2 m = make_uint2(0u, 0u);
         if (t <= tstop) m = R.meta[base + t - 1];
         const bool in_win = t <= tstop;
-        const bool outside = in_win && m.y != 0u;
+        const bool outside = in_win && (m.y & 1u) != 0u;
         const bool saved = in_win && (!outside || D.pick_all) && t >= ts0;
         const unsigned smask = __ballot_sync(0xffffffffu, saved);
         const int cnt = count + __popc(smask & ((1u << lane) - 1u)) + 1;
         const bool acc = saved && (D.keep_last || ((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(cnt)) >> 32) == 0);
         const unsigned amask = __ballot_sync(0xffffffffu, acc);
         const unsigned omask = __ballot_sync(0xffffffffu, outside);
+        const unsigned fmask = __ballot_sync(0xffffffffu, in_win && (m.y & 2u) != 0u);
         if (amask) {
             const int hl = 31 - __clz(amask);
             pick = t0 + hl;
@@ -917,6 +921,7 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         }
         count += __popc(smask);
         nout += __popc(omask);
+        nfold += __popc(fmask);
     }
     if (pick_out) pick = 0;  // rejected: the walker keeps its start point
     const int slot = C.order[D.pt_off + w];
@@ -929,7 +934,8 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(tstop - nout));
         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
-        if (pick <= 0) C.wint[(D.w_off + w) * 8 + 6] = 1;
+        if (nfold) atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_fold), static_cast<unsigned long long>(nfold));
+        if (pick <= 0) C.wint[(D.w_off + w) * WINT + 6] = 1;
     }
 }
 

@@ -41,17 +41,20 @@ __device__ __forceinline__ void wrap_periodic(const RunDesc &D, const ParView &P
 // (the path unfolded on a line of period 2w folds into the box; an odd number of
 // crossings flips that momentum component), so the walker never leaves the prior
 // and the box takes no outside step.  Padded components (lo = hi = x = 0) never fold.
-// SWZ: lo and hi are in the lane-row layout (one-walker-per-warp kernels).
+// SWZ: lo and hi are in the lane-row layout (one-walker-per-warp kernels).  Returns
+// whether one of this lane's components folded.
 template <int KIND, int E, bool SWZ = false>
-__device__ __forceinline__ void fold_box(const RunDesc &D, const ParView &P, float (&x)[E], float (&p)[E], int c0)
+__device__ __forceinline__ bool fold_box(const RunDesc &D, const ParView &P, float (&x)[E], float (&p)[E], int c0)
 {
+    bool folded = false;
     if constexpr (KIND != NS_LIK_TORUS) {
-        if (!D.box_fold) return;
+        if (!D.box_fold) return false;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int c = SWZ ? swz_col<E>(c0 + e) : c0 + e;
             const float lo = P.lo[c], hi = P.hi[c];
             if (!(x[e] < lo || x[e] > hi)) continue;
+            folded = true;
             const float w = hi - lo, w2 = 2.f * w;
             float u = x[e] - lo;
             u -= w2 * floorf(u / w2);
@@ -65,6 +68,7 @@ __device__ __forceinline__ void fold_box(const RunDesc &D, const ParView &P, flo
             }
         }
     }
+    return folded;
 }
 
 // Copy the parameter block of run D into shared memory (the precision matrix
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
     float x[E], p[E], xr[E], g[E], eps[E], vmask[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) vmask[e] = (c0 + e < D.d) ? 1.f : 0.f;  // padded components keep p = 0
-    int w = 0, t = 0, nref = 0, consec = 0, count = 0, nin = 0, nout = 0;
+    int w = 0, t = 0, nref = 0, consec = 0, count = 0, nin = 0, nout = 0, nfold = 0;
     int res_start = 0;  // the reservoir holds a rejected (outside) step: emit the start point
     float res_ll = 0.f;
     bool active = false, exhausted = false;
@@ -734,7 +738,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         if (c0 + e >= D.d) p[e] = 0.f;
                         xr[e] = x[e];
                     }
-                    t = nref = consec = count = nin = nout = res_start = 0;
+                    t = nref = consec = count = nin = nout = nfold = res_start = 0;
                     res_ll = 0.f;
                     // archive the dead point that this walker's output will replace
                     const int ks = C.order[D.pt_off + w];
@@ -750,9 +754,10 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         p[e] = ws[dp + e];
                         xr[e] = ws[2 * dp + e];
                     }
-                    const int *wi = C.wint + (D.w_off + w) * 8;
+                    const int *wi = C.wint + (D.w_off + w) * WINT;
                     t = wi[0]; nref = wi[1]; consec = wi[2]; count = wi[3]; nin = wi[4]; nout = wi[5];
                     res_start = wi[7];
+                    nfold = wi[8];
                     res_ll = C.wres_logl[D.w_off + w];
                 }
             }
@@ -773,9 +778,10 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         ws[2 * dp + e] = xr[e];
                     }
                     if (lig == 0) {
-                        int *wi = C.wint + (D.w_off + w) * 8;
+                        int *wi = C.wint + (D.w_off + w) * WINT;
                         wi[0] = t; wi[1] = nref; wi[2] = consec; wi[3] = count; wi[4] = nin; wi[5] = nout;
                         wi[7] = res_start;
+                        wi[8] = nfold;
                         C.wres_logl[D.w_off + w] = res_ll;
                         if (phase == 0) atomicMax(&S->t_save, (nref >= D.min_ref) ? t : D.n_steps + 1);
                         else atomicMax(&S->t_stop, t);
@@ -802,7 +808,8 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                         C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
                         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(nin));
                         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));
-                        if (count == 0 || res_start) C.wint[(D.w_off + w) * 8 + 6] = 1;
+                        if (nfold) atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_fold), static_cast<unsigned long long>(nfold));
+                        if (count == 0 || res_start) C.wint[(D.w_off + w) * WINT + 6] = 1;
                     }
                 }
                 active = false;
@@ -822,7 +829,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
-        fold_box<KIND, E>(D, P, x, p, c0);
+        const bool lfold = fold_box<KIND, E>(D, P, x, p, c0);
         const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
         int outbox = 0;
         float nb[E];
@@ -833,7 +840,10 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
             nb[e] = (x[e] < P.lo[c]) ? -1.f : ((x[e] > P.hi[c]) ? 1.f : 0.f);
             outbox += (nb[e] != 0.f);
         }
-        outbox = gsum_i<G>(outbox);
+        // the box count and the fold flag (bit 16) in one group sum
+        outbox = gsum_i<G>(outbox | (lfold ? 0x10000 : 0));
+        const bool folded = (outbox >> 16) != 0;
+        outbox &= 0xffff;
         const bool outside = (outbox > 0) || !(ll > lstar);
         float pnb = 0.f, pg = 0.f, gg = 0.f;
         if (__any_sync(0xffffffffu, stepping && outside)) {
@@ -875,7 +885,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
         }
         if (stepping) {
             nref += outside ? 1 : 0;
-            if (outside) { ++nout; ++consec; } else { ++nin; consec = 0; }
+            if (outside) { ++nout; ++consec; } else { ++nin; consec = 0; nfold += folded ? 1 : 0; }
         }
         // trajectory preservation: size-1 reservoir over the steps of the saving window
         // (inside steps only; with pick_all every step, a drawn outside step rejecting)
@@ -1153,7 +1163,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
-        fold_box<KIND, E, COOP>(D, P, x, p, c0);
+        const bool lfold = fold_box<KIND, E, COOP>(D, P, x, p, c0);
         float ll;
         if constexpr (TC) {
             ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok);
@@ -1194,7 +1204,10 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             pg = fmaf(p[e], g[e], pg);
             gg = fmaf(g[e], g[e], gg);
         }
-        outbox = gsum_i<G>(outbox);
+        // the box count and the fold flag (bit 16) in one group sum
+        outbox = gsum_i<G>(outbox | (lfold ? 0x10000 : 0));
+        const bool folded = (outbox >> 16) != 0;
+        outbox &= 0xffff;
         pnb = gsum<G>(pnb);
         pg = gsum<G>(pg);
         gg = gsum<G>(gg);
@@ -1247,7 +1260,8 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             // record the step
             if (!outside) row_store<E>(rec_x, x);
             if (lig == 0) {
-                *rec_meta = make_uint2(res_word, outside ? 1u : 0u);
+                // flags: bit 0 outside, bit 1 an inside step on which the box reflected the walker
+                *rec_meta = make_uint2(res_word, outside ? 1u : (folded ? 2u : 0u));
                 *rec_ll = ll;
             }
             rec_x += R.xs;

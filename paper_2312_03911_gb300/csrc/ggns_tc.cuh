@@ -79,6 +79,32 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// Non-blocking test of the phase of `bar` with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// As mbar_wait, polling without suspending the thread: for the single lanes that feed
+// the tensor cores, whose other warp-mates wait at a warp barrier.
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > WAIT_NS) return false;
+    }
+}
+
 // Wait for the phase of `bar` with the given parity to complete; false if it did not
 // within WAIT_NS nanoseconds.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
@@ -327,7 +353,7 @@ __device__ inline void issue_mmas(const State &T, Pipe &pp)
     uint32_t par = pp.full_par;
 #pragma unroll 1
     for (int i = 0; i < NPOS; ++i) {
-        if (failed(T) || !mbar_wait(full + s, par)) {
+        if (failed(T) || !mbar_poll(full + s, par)) {
             *T.fail = 1;
             return;
         }
@@ -370,7 +396,7 @@ __device__ inline void refill_stage(const State &T, Pipe &pp, int w)
 {
     int idx = STAGES + (w - pp.s0 + STAGES) % STAGES;
     for (; idx < T.npos + STAGES; idx += STAGES) {
-        if (failed(T) || !mbar_wait(T.empty + w, pp.empty_par)) {
+        if (failed(T) || !mbar_poll(T.empty + w, pp.empty_par)) {
             *T.fail = 1;
             return;
         }

@@ -45,7 +45,7 @@ class Config(C.Structure):
                 ("noise_mode", C.c_int), ("out_lo", C.c_double), ("out_hi", C.c_double), ("seed", C.c_uint64),
                 ("run_id", C.c_uint32), ("max_iters", C.c_long), ("dead_cap", C.c_long),
                 ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int), ("keep_last", C.c_int),
-                ("box_fold", C.c_int),
+                ("box_fold", C.c_int), ("fold_counts", C.c_int),
                 ("tile", C.c_int), ("hss_mode", C.c_int), ("rec_len", C.c_int), ("noise_ahead", C.c_int),
                 ("coop", C.c_int), ("runs_per_group", C.c_int)]
 
@@ -284,10 +284,10 @@ class Sampler:
                                       _vp(stream)), self.h)
 
     def hss(self, x0_ptr, logl0_ptr, n, lstar, dt, it, x_out_ptr, logl_out_ptr, steps_ptr=None, stream=None):
-        st = (C.c_long * 4)()
+        st = (C.c_long * 5)()
         _check(load().ns_hss(self.h, _vp(x0_ptr), _vp(logl0_ptr), int(n), float(lstar), float(dt), int(it),
                              _vp(x_out_ptr), _vp(logl_out_ptr), _vp(steps_ptr), st, _vp(stream)), self.h)
-        return dict(n_in=st[0], n_out=st[1], t_save=st[2], t_stop=st[3])
+        return dict(n_in=st[0], n_out=st[1], t_save=st[2], t_stop=st[3], n_fold=st[4])
 
 
 def philox(ctr_ptr, key0, key1, out_ptr, n, stream=None):

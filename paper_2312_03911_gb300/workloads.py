@@ -37,15 +37,24 @@ LIK_ISO, LIK_MIX_ISO, LIK_DENSE, LIK_DENSE_MIX, LIK_ROSEN, LIK_TORUS = 0, 1, 2, 
 # over the steps of its saving window, a drawn outside step returning the start
 # point; with several clusters alive a new point that lands nearer another
 # cluster's survivors returns its start point.  Leaving the prior box is an
-# outside step (box_fold = 1, an exact reflection off the faces, is an option).
+# outside step.  The exact reflection (the position folds back across the face and
+# that momentum component flips: box_fold = 1, without counting the folds for the
+# step size) is what the high-dimensional dense workloads c3 and c5 use: there the
+# slices meet the faces through much of the run, box steps dominate the outside
+# fraction, dt collapses and log Z falls tens of nats low at d = 512 (-60), while
+# the exact reflection stays within a few nats.  Counting the folds for the step
+# size (fold_counts = 1) is unbiased up to d = 128 but collapses dt at d = 512,
+# where some coordinate is near a face on almost every step.
 # The printed forms (multiplicative noise with dp = 0.05 on every step, the pick
 # among inside states only) remain selectable: PAPER_NOISE and PRINTED_PICK.
 DEFAULT_CFG = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.5, tol=0.01, min_ref=1,
                    max_ref=3, prune_after=10, termination=0, clustering=1, seed=0, run_id=0,
                    max_iters=100000, noise_mode=1, out_lo=0.05, out_hi=0.15, noise_inside=1, pick_all=1,
-                   territory=1, box_fold=0)
+                   territory=1, box_fold=0, fold_counts=0)
 PAPER_NOISE = dict(noise_mode=0, delta_p=0.05, noise_inside=0)
 PRINTED_PICK = dict(pick_all=0, territory=0)
+BOX_FOLD = dict(box_fold=1, fold_counts=0)
+BOX_FOLD_COUNTED = dict(box_fold=1, fold_counts=1)
 
 
 def _rng(seed):
@@ -95,7 +104,7 @@ def workload(name: str, seed: int | None = None, **over):
         lo, hi = -np.ones(d), np.ones(d)
         # one mode: clustering off (Algorithm 4 on this anisotropic d=128 cloud splits it
         # into more than 64 k-NN components within 18 iterations)
-        cfg = dict(DEFAULT_CFG, n_live=2000, clustering=0)
+        cfg = dict(DEFAULT_CFG, n_live=2000, clustering=0, **BOX_FOLD)
         base = SEED_BASE + 3
     elif name == "c5":
         d, K = 512, 8
@@ -107,7 +116,7 @@ def workload(name: str, seed: int | None = None, **over):
         # clustering off as for c3; dt starts at 0.01: from 0.1 every step of this narrow d=512
         # posterior leaves the slice, the walkers return their start points and the XL peak
         # on the stalled L* ended the run after 18 iterations
-        cfg = dict(DEFAULT_CFG, n_live=4000, clustering=0, dt_init=0.01)
+        cfg = dict(DEFAULT_CFG, n_live=4000, clustering=0, dt_init=0.01, **BOX_FOLD)
         base = SEED_BASE + 5
     else:
         raise KeyError(name)

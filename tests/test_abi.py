@@ -36,7 +36,7 @@ def test_config_defaults_without_gpu():
         (200, 1000, 1, 3, 0, 1, 1)
     assert c.tol == pytest.approx(0.01) and c.dt_init == pytest.approx(0.1) and c.delta_p == pytest.approx(0.5)
     # the readings of Algorithm 5 the library defaults to, and the library's own launch choices
-    assert (c.noise_inside, c.pick_all, c.territory, c.keep_last, c.box_fold) == (1, 1, 1, 0, 0)
+    assert (c.noise_inside, c.pick_all, c.territory, c.keep_last, c.box_fold, c.fold_counts) == (1, 1, 1, 0, 0, 0)
     assert (c.tile, c.hss_mode, c.rec_len, c.noise_ahead, c.coop, c.runs_per_group) == (0, 0, 0, 0, 0, 0)
 
 

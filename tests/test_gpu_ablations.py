@@ -52,7 +52,8 @@ def _agree(zg, zo, floor):
 
 
 # (name, configuration overrides): Appendix G's fixed step sizes, no momentum noise, the classic
-# termination, the fixed-step keep-last sampler, and Algorithm 5's printed noise and pick
+# termination, the fixed-step keep-last sampler, Algorithm 5's printed noise and pick, and the two
+# other readings of the prior box
 VARIANTS = [
     ("fixed dt 0.1", dict(dt_init=0.1, out_lo=0.0, out_hi=1.0)),
     ("fixed dt 0.5", dict(dt_init=0.5, out_lo=0.0, out_hi=1.0)),
@@ -62,6 +63,7 @@ VARIANTS = [
     ("printed noise", dict(noise_mode=0, delta_p=0.05)),
     ("printed noise and pick", dict(noise_mode=0, delta_p=0.05, noise_inside=0, pick_all=0, territory=0)),
     ("exact box reflection", dict(box_fold=1)),
+    ("exact box reflection, folds counted for dt", dict(box_fold=1, fold_counts=1)),
 ]
 
 
@@ -72,7 +74,8 @@ def test_ablation_variant_matches_oracle(name, over):
     s, res = _gpu(w, 16)
     assert all(r["status"] == 0 for r in res), [r["status"] for r in res]
     zg = np.array([r["logz"] for r in res])
-    zo = np.array([o["logz"] for o in _orc(w, list(range(100, 108)))])
+    # 16 oracle seeds: with 8 the sample spread understates the scatter of these short runs
+    zo = np.array([o["logz"] for o in _orc(w, list(range(100, 116)))])
     ok, info = _agree(zg, zo, 0.25)
     assert ok, (name, info)
     # the likelihood evaluations per run agree too (same trajectory rules on both sides)
