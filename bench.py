@@ -397,10 +397,10 @@ def gpu_arm(args):
         tensor = prof.get("tensor_classes", 0) > 0
         achieved = flops * sum(pts) / hss_s if hss_s > 0 else None
         if tensor:
-            # TF32 tcgen05: the measured BF16 peak (sustained: the kernel runs inside a long step)
-            # times the nominal TF32/BF16 ratio 1/2
-            peak = 0.5 * float(peaks.get("bf16_tflops_sustained") or 1700.0) * 1e12
-            bound, pnote = "tensor", "TF32 = measured BF16 sustained x 1/2 (nominal dtype ratio)"
+            # FP16 tcgen05 (kind::f16): the measured BF16 peak, sustained (the kernel runs inside a
+            # long step); FP16 and BF16 share the nominal dense rate
+            peak = float(peaks.get("bf16_tflops_sustained") or 1700.0) * 1e12
+            bound, pnote = "tensor", "FP16 = measured BF16 sustained (same nominal dense rate)"
         else:
             peak = SMS * FP32_LANES_PER_SM * 2.0 * f_sm
             bound, pnote = "alu", f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {f_sm / 1e6:.0f} MHz"

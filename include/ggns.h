@@ -186,7 +186,7 @@ ns_status ns_restart(ns_ctx *ctx, uint64_t seed);
  * of momentum noise drawn ahead per walker (0: drawn during the walk), out[8]
  * walker classes stepping CTA-cooperatively (dense likelihoods whose precision
  * matrix is read from global memory in shared tiles), out[9] those of them whose
- * contraction runs on the tensor cores (tcgen05, 3xTF32).
+ * contraction runs on the tensor cores (tcgen05 kind::f16, a scaled two-term FP16 split).
  * reset != 0 zeroes out[0..4] after reading.  Synchronises. */
 ns_status ns_profile(const ns_ctx *ctx, double *out, int reset);
 

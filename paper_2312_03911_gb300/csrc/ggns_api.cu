@@ -275,7 +275,7 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
 
 // Parameter block of one run (FP32 copy of the FP64 inputs, see ParLayout).
 ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int d_pad, std::vector<float> &out,
-                       float &lik_const)
+                       float &lik_const, float &tc_sv, float &tc_inv)
 {
     const int d = b.d, K = kind_has_means(lk.kind) ? lk.n_comp : 1;
     const ParLayout L = par_layout(d, d_pad, K, lk.kind);
@@ -286,6 +286,7 @@ ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int 
     }
     const double log2pi = 1.8378770664093454836;
     lik_const = 0.f;
+    tc_sv = tc_inv = 1.f;
     if (!kind_has_means(lk.kind)) return NS_OK;
     for (int k = K; k < comp_slots(K, lk.kind); ++k) out[L.comp_b + k] = -INFINITY;  // padding: weight 0
     for (int k = 0; k < K; ++k)
@@ -316,29 +317,38 @@ ns_status build_params(const ns_prior_box &b, const ns_likelihood_spec &lk, int 
                 }
         }
         if (tc_layout(lk.kind, d_pad)) {
-            // P = P_hi + P_lo, both TF32 (10-bit mantissas, rounded to nearest, ties away from
-            // zero); K-step j of 8 columns holds, for each 128-row tile m, the rows in core
-            // matrices of 8 rows x 4 columns: row r, column kk at (r/8) 64 + (kk/4) 32 + (r%8) 4 + kk%4
-            auto tf32 = [](float v) {
-                uint32_t u;
-                memcpy(&u, &v, 4);
-                u = (u + 0x1000u) & 0xFFFFE000u;
-                float r;
-                memcpy(&r, &u, 4);
-                return r;
-            };
-            const int mt = d_pad / 128, ks = d_pad / 8;
+            // s_p P = P1 + 2^-11 P2 in FP16: s_p = 2^ep puts the largest |P_ij| just below 2^13,
+            // P1 is s_p P rounded to nearest, P2 the remainder times 2^11 rounded to nearest.
+            // The walkers scale v by s_v = 2^ev, chosen so that |v| up to twice the box's largest
+            // coordinate stays below 2^13 (v = x - mu, or x for the mixture).  K-step j of 16
+            // columns holds, for each 128-row tile m, the rows in core matrices of 8 rows x 8
+            // columns: row r, column kk at half (r/8) 128 + (kk/8) 64 + (r%8) 8 + kk%8.
+            double pmax = 0.0, bmax = 0.0;
+            for (size_t i = 0; i < (size_t)d * d; ++i) pmax = std::max(pmax, std::fabs(lk.precision[i]));
+            for (int i = 0; i < d; ++i) bmax = std::max(bmax, std::max(std::fabs(b.lo[i]), std::fabs(b.hi[i])));
+            int e_p = 0, e_v = 0;
+            std::frexp(pmax, &e_p);  // pmax < 2^e_p
+            std::frexp(bmax > 0.0 ? 2.0 * bmax : 1.0, &e_v);
+            const int ep = 13 - e_p, ev = 13 - e_v;
+            if (ep + ev < -100 || ep + ev > 100)
+                return fail(nullptr, NS_ERR_ARG, "precision or box out of the range of the tensor-core split");
+            tc_sv = (float)std::ldexp(1.0, ev);
+            tc_inv = (float)std::ldexp(1.0, -(ep + ev));
+            __half *h = reinterpret_cast<__half *>(out.data() + L.ptc);
+            const int mt = d_pad / 128, ks = d_pad / 16;
             for (int j = 0; j < ks; ++j)
                 for (int m = 0; m < mt; ++m)
                     for (int r = 0; r < 128; ++r)
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const int row = m * 128 + r, col = 8 * j + kk;
-                            const float p = (row < d && col < d) ? (float)lk.precision[(size_t)row * d + col] : 0.f;
-                            const float hi = tf32(p), lo = tf32(p - hi);
-                            const long at = (r / 8) * 64 + (kk / 4) * 32 + (r % 8) * 4 + (kk % 4);
-                            const long blk = (long)j * 2 * mt * 1024;
-                            out[L.ptc + blk + (long)m * 1024 + at] = hi;
-                            out[L.ptc + blk + (long)mt * 1024 + (long)m * 1024 + at] = lo;
+                        for (int kk = 0; kk < 16; ++kk) {
+                            const int row = m * 128 + r, col = 16 * j + kk;
+                            const double p =
+                                (row < d && col < d) ? std::ldexp(lk.precision[(size_t)row * d + col], ep) : 0.0;
+                            const __half p1 = __double2half(p);
+                            const __half p2 = __double2half(std::ldexp(p - (double)__half2float(p1), 11));
+                            const long at = (r / 8) * 128 + ((kk / 8) * 64) + (r % 8) * 8 + (kk % 8);
+                            const long blk = (long)j * 2 * mt * 2048;
+                            h[blk + (long)m * 2048 + at] = p1;
+                            h[blk + (long)mt * 2048 + (long)m * 2048 + at] = p2;
                         }
         }
     }
@@ -682,7 +692,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.key0 = (uint32_t)c.seed;
         D.key1 = (uint32_t)(c.seed >> 32) ^ rid;
         D.max_iters = c.max_iters;
-        ns_status s = build_params(box[r], lik[r], D.d_pad, pars[r], D.lik_const);
+        ns_status s = build_params(box[r], lik[r], D.d_pad, pars[r], D.lik_const, D.tc_sv, D.tc_inv);
         if (s != NS_OK) {
             delete ctx;
             return s;

@@ -61,6 +61,7 @@ struct RunDesc {
                                                        // reflections in the step-size control
     float delta_p, keep, rosen_scale, lik_const;
     float torus_a, torus_b, torus_c;  // TORUS: sine and cosine frequencies, offset
+    float tc_sv, tc_inv;              // tensor-core contraction: scale s_v of v, 1 / (s_p s_v)
     double log_tol, out_lo, out_hi, dt_init;
     uint32_t key0, key1;
     long max_iters;
@@ -89,9 +90,10 @@ struct RunDesc {
 struct ParLayout {
     long lo, hi, means, comp_a, comp_b, prec, pmu, ptc, total;
 };
-// Dense kinds whose d_pad is 128, 256 or 512 also carry P pre-split into TF32 pairs and
-// laid out for the tensor cores (ggns_tc.cuh): d_pad/8 K-steps x (P_hi, P_lo) x d_pad/128
-// tiles of 128 rows x 8 columns in core-matrix order (2 d_pad^2 floats, global memory only).
+// Dense kinds whose d_pad is 128, 256 or 512 also carry P scaled by a power of two s_p and
+// pre-split into FP16 pairs s_p P = P1 + 2^-11 P2, laid out for the tensor cores
+// (ggns_tc.cuh): d_pad/16 K-steps x (P1, P2) x d_pad/128 tiles of 128 rows x 16 columns in
+// core-matrix order (d_pad^2 floats' worth of FP16, global memory only).
 __host__ __device__ inline bool tc_layout(int kind, int d_pad)
 {
     return (kind == NS_LIK_DENSE_GAUSS || kind == NS_LIK_DENSE_MIX) && d_pad % 128 == 0 && d_pad <= 512;
@@ -128,7 +130,7 @@ __host__ __device__ inline ParLayout par_layout(int d, int d_pad, int n_comp, in
     if (kind == NS_LIK_DENSE_MIX) o += (long)n_comp * d_pad;
     o = (o + 3) & ~3L;  // 16-byte aligned: the tensor-core layout is read by bulk copies
     L.ptc = o;
-    if (tc_layout(kind, d_pad)) o += 2l * d_pad * d_pad;
+    if (tc_layout(kind, d_pad)) o += 1l * d_pad * d_pad;
     L.total = (o + 3) & ~3L;
     return L;
 }

@@ -600,7 +600,7 @@ __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&
         }
     }
     float y[E];
-    ok = tc::contract<E>(T, pp, g, D.d_pad, y);
+    ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, y);
     return dense_finish<KIND, 32, E, true>(D, P, x, y, g, c0, nullptr);
 }
 
@@ -1347,6 +1347,16 @@ __global__ void __launch_bounds__(HSS_THREADS) k_lik_points(DevCtx C, int run, c
             }
             if (want_mu) {
                 const int K = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1 : D.n_comp;
+                if constexpr (KIND == NS_LIK_DENSE_MIX) {
+                    // the mixture shares P and the responsibilities sum to one, so the score
+                    // -g = y - sum_k resp_k P mu_k gives y = P x back without a second product
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        float t = -g[e];
+                        for (int k = 0; k < K; ++k) t = fmaf(resp[k], P.pmu[(long)k * D.d_pad + c0 + e], t);
+                        g[e] = t;
+                    }
+                }
                 for (int k = 0; k < K; ++k) {
                     const float rk = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1.f : resp[k];
 #pragma unroll
@@ -1359,11 +1369,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_lik_points(DevCtx C, int run, c
                         } else if (KIND == NS_LIK_DENSE_GAUSS) {
                             v = -g[e];  // P (x - mu)
                         } else {
-                            // P (x - mu_k) = P x - P mu_k; recover P x from the gradient identity
-                            // is not possible for a mixture, so recompute it row by row
-                            float y = 0.f;
-                            for (int j = 0; j < D.d; ++j) y = fmaf(P.prec[(long)j * D.d_pad + c], xin[ii * D.d + j], y);
-                            v = y - P.pmu[(long)k * D.d_pad + c];
+                            v = g[e] - P.pmu[(long)k * D.d_pad + c];  // P (x - mu_k) = y - P mu_k
                         }
                         atomicAdd(&gmu[(long)k * D.d + c], go * rk * v);
                     }
@@ -1376,6 +1382,11 @@ __global__ void __launch_bounds__(HSS_THREADS) k_lik_points(DevCtx C, int run, c
 // ------------------------------------------------------------------------
 // Posterior-weighted parameter gradient over the dead arena (partials).
 // part[blk][K][d] (FP64) += sum_i p_i resp_ik v_ik, p_i = exp(logw_i + logL_i - logZ).
+// Dead points with p_i < e^-60 are skipped (warps whose points all fall below it skip
+// the likelihood): together they move the sum by less than n_dead e^-60 max |v|, far
+// below its FP64 rounding.  For the dense mixture v_ik = P (x_i - mu_k) = y_i - P mu_k
+// comes from the score the likelihood returns, -g_i = y_i - sum_j resp_ij P mu_j, so
+// y_i = P x_i is formed once per point, not once per component.
 // ------------------------------------------------------------------------
 template <int KIND, int G, int E>
 __global__ void __launch_bounds__(HSS_THREADS) k_grad_means(DevCtx C, int run, double logz, double *part,
@@ -1403,16 +1414,27 @@ __global__ void __launch_bounds__(HSS_THREADS) k_grad_means(DevCtx C, int run, d
         const long i = base + grp;
         const bool act = i < n;
         const long ii = act ? i : 0;
+        const double lp = act ? (D.dead_logw[D.dead_off + ii] + (double)D.dead_logl[D.dead_off + ii] - logz)
+                              : -INFINITY;
+        const bool keep = lp > -60.0;
+        if (!__any_sync(0xffffffffu, keep)) continue;  // the likelihood's group sums are warp-wide
         const float *src = D.dead_x + (D.dead_off + ii) * D.d_pad + c0;
         float x[E], g[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) x[e] = src[e];
         lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, resp);
-        if (!act) continue;
-        const double lp = D.dead_off >= 0 ? (D.dead_logw[D.dead_off + ii] + (double)D.dead_logl[D.dead_off + ii] - logz)
-                                          : -INFINITY;
+        if (!keep) continue;
         const double pw = exp(lp);
-        if (!(pw > 0.0)) continue;
+        if constexpr (KIND == NS_LIK_DENSE_MIX) {
+            // y - sum_j resp_j P mu_j = -g; add the weighted P mu back once
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int c = c0 + e;
+                float t = -g[e];
+                for (int k = 0; k < K; ++k) t = fmaf(resp[k], P.pmu[(long)k * D.d_pad + c], t);
+                g[e] = t;  // y
+            }
+        }
         for (int k = 0; k < K; ++k) {
             const float rk = (KIND == NS_LIK_ISO_GAUSS || KIND == NS_LIK_DENSE_GAUSS) ? 1.f : resp[k];
 #pragma unroll
@@ -1425,9 +1447,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_grad_means(DevCtx C, int run, d
                 } else if (KIND == NS_LIK_DENSE_GAUSS) {
                     v = -g[e];
                 } else {
-                    float y = 0.f;
-                    for (int j = 0; j < D.d; ++j) y = fmaf(P.prec[(long)j * D.d_pad + c], D.dead_x[(D.dead_off + ii) * D.d_pad + j], y);
-                    v = y - P.pmu[(long)k * D.d_pad + c];
+                    v = g[e] - P.pmu[(long)k * D.d_pad + c];
                 }
                 atomicAdd(&acc[k * D.d + c], pw * (double)rk * (double)v);
             }

@@ -2,29 +2,37 @@
 // dense-mixture likelihoods on the fifth-generation tensor cores (tcgen05).
 //
 // One CTA steps 16 walkers (one per warp).  Each step, the walkers' vectors v
-// (x - mu, or x for the mixture) are split into TF32 pairs v = v_hi + v_lo and
-// written to shared memory as the B operand (N = 16 walkers, K-major core
-// matrices).  The precision matrix, pre-split into P_hi + P_lo and pre-laid-out in
+// (x - mu, or x for the mixture) are scaled by a power of two s_v and split into
+// FP16 pairs s_v v = V1 + 2^-11 V2, written to shared memory as the B operand
+// (N = 16 walkers, K-major core matrices).  The precision matrix, scaled by a power
+// of two s_p and split the same way (s_p P = P1 + 2^-11 P2) and pre-laid-out in
 // core-matrix order when the context is created, streams from global memory through
-// a ring of STAGES shared-memory stages of 32 KB (a stage holds P_hi and P_lo of one
-// K-step of 8 columns for every 128-row M-tile, or of several K-steps when d_pad is
-// small).  Lane 0 of warp 0 issues, per half, the MMAs of the 3xTF32 product
-// P_hi v_hi + P_hi v_lo + P_lo v_hi (M = 128, N = 16, K = 8, FP32 accumulation in
-// tensor memory: the three products in accumulators of their own, so that an MMA
-// never waits for the one issued just before it; they are added in the read-back)
-// and commits each stage's MMAs to that stage's `empty` barrier.
+// a ring of STAGES shared-memory stages of 32 KB (a stage holds P1 and P2 of one
+// K-step of 16 columns for every 128-row M-tile, or of several K-steps when d_pad is
+// small).  Lane 0 of warp 0 issues, per half, the MMAs of the products P1 V1,
+// P1 V2 and P2 V1 (kind::f16, M = 128, N = 16, K = 16, FP32 accumulation in tensor
+// memory: the three products in accumulators of their own, so that an MMA never
+// waits for the one issued just before it) and commits each stage's MMAs to that
+// stage's `empty` barrier.  The read-back forms
+//     y = (P1 V1 + 2^-11 (P1 V2 + P2 V1)) / (s_p s_v),
+// whose neglected term 2^-22 P2 V2 and the split's rounding leave y within about
+// 2^-22 of |P| |v| (each factor carries 22 significant bits; the scales keep every
+// FP16 value in the normal range of its own magnitude).  Against a split into TF32
+// pairs this halves the bytes of P streamed per step and the B operand in shared
+// memory, and it runs at the FP16 rate.
 // Stage s is refilled by lane 0 of warp 1 + s with a 1-D bulk copy once the MMAs
 // that read it are done: an SM completes the bulk copies of one issuing warp one
 // after another, so the copies of several warps are what keeps enough bytes in
 // flight to cover the latency of the L2.  The accumulators, Y^T[d_pad][16] (P is
 // symmetric, so Y^T = P V^T), are read back with tcgen05.ld and handed to the
-// walkers through shared memory.  The split keeps the product at FP32 accuracy
-// (the neglected P_lo v_lo is 2^-22 relative).
+// walkers through shared memory.
 //
 // Every wait is bounded (2 s): a wait that gives up sets the CTA's failure flag,
 // the run's status NS_ERR_TIMEOUT, and the kernel winds down, waiting (again
 // bounded) for its MMAs and copies in flight and freeing its tensor memory.
 #pragma once
+
+#include <cuda_fp16.h>
 
 #include "ggns_internal.cuh"
 
@@ -32,7 +40,7 @@ namespace ggns {
 namespace tc {
 
 constexpr int WALKERS = 16;                    // N of every MMA: one walker per warp of a 512-thread CTA
-constexpr int STAGES = 3;                      // shared-memory stages of P (one producer warp each)
+constexpr int STAGES = 4;                      // shared-memory stages of P (one producer warp each)
 constexpr uint32_t STAGE_BYTES = 32768;        // bytes of one stage
 constexpr uint64_t WAIT_NS = 2000000000ull;    // a wait gives up after 2 s
 
@@ -41,11 +49,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float v)
+// Two FP16 values in one 32-bit word (lo at the lower address).
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
@@ -142,22 +150,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t instr_desc_tf32(int M, int N)
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B FP16 (format 0 in
+// bits 7-9 and 10-12), both K-major, dense, N / 8 in bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t instr_desc_f16(int M, int N)
 {
-    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-           (static_cast<uint32_t>(M >> 4) << 24);
+    return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // (No memory clobber: the operands were published by the barriers and fences before
 // the MMAs; keeping shared-memory reads of the issuing loop in registers across the
 // MMAs is what lets one lane issue them back to back.)
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
@@ -183,19 +191,18 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// The B operand of K-step j (its 16 walkers x 8 columns, 512 bytes) starts at byte
-// vpos(j) of V_hi / V_lo.  A lane writes its E columns as quads into K-steps
-// lane E / 8 ..; one extra 16 bytes after every R = max(E / 8, 1) K-steps puts the
-// quads that the eight lanes of a quarter-warp write into distinct bank groups.
-__host__ __device__ constexpr int vgroup(int d_pad) { return d_pad >= 256 ? d_pad / 256 : 1; }
-__host__ __device__ constexpr uint32_t vpos(int j, int r) { return 512u * j + 16u * (j / r); }
+// The B operand of K-step j (its 16 walkers x 16 FP16 columns, 512 bytes) starts at
+// byte vpos(j) of V1 / V2: one extra 16 bytes after every K-step puts the 16-byte
+// rows that the lanes of a quarter-warp write (a lane's E columns lie in K-step
+// lane E / 16) into distinct bank groups.
+__host__ __device__ constexpr uint32_t vpos(int j) { return 528u * j; }
 
 // Layout of the tensor-core state in dynamic shared memory (bytes from a 1024-aligned base).
 struct Plan {
-    int mt, ks, vr;          // 128-row M-tiles, 8-column K-steps of d_pad, K-steps per lane row
+    int mt, ks;              // 128-row M-tiles, 16-column K-steps of d_pad
     int units;               // halves (P_hi or P_lo of one K-step, mt x 4 KB) per stage
     int npos;                // stages consumed by one contraction (2 ks / units)
-    uint32_t vbytes;         // one B operand (V_hi or V_lo)
+    uint32_t vbytes;         // one B operand (V1 or V2)
     uint32_t v_off, stage_off, bar_off, total;
 };
 
@@ -203,36 +210,35 @@ __host__ __device__ inline Plan plan(int d_pad)
 {
     Plan p;
     p.mt = d_pad / 128;
-    p.ks = d_pad / 8;
-    p.vr = vgroup(d_pad);
+    p.ks = d_pad / 16;
     p.units = static_cast<int>(STAGE_BYTES / (4096u * p.mt));
     p.npos = 2 * p.ks / p.units;
-    p.vbytes = (vpos(p.ks, p.vr) + 127u) & ~127u;
-    p.v_off = 0;                                            // V_hi then V_lo
+    p.vbytes = (vpos(p.ks) + 127u) & ~127u;
+    p.v_off = 0;                                            // V1 then V2
     p.stage_off = p.v_off + 2 * p.vbytes;
     p.bar_off = p.stage_off + STAGES * STAGE_BYTES;         // full[S], empty[S], done, tmem base
     p.total = p.bar_off + (2 * STAGES + 1) * 8 + 16;
     return p;
 }
 
-// Floats of the pre-laid-out P of a run: ks K-steps x (P_hi, P_lo) x mt tiles x 1024.
-__host__ __device__ inline long ptc_floats(int d_pad) { return 2l * d_pad * d_pad; }
+// Floats of the pre-laid-out P of a run: ks K-steps x (P1, P2) x mt tiles x 4 KB of FP16.
+__host__ __device__ inline long ptc_floats(int d_pad) { return 1l * d_pad * d_pad; }
 
 // Per-CTA state (shared-memory pointers, tensor-memory base), kept in shared memory:
 // thread 0 writes it, every thread reads it.
 struct State {
-    float *vhi, *vlo;     // B operand (Y^T aliases vhi after the MMAs)
+    float *vhi, *vlo;     // B operands V1 and V2 (Y^T aliases both after the MMAs)
     char *stages;
     uint64_t *full, *empty, *done;
     uint32_t *tmem_slot;
     uint32_t tmem;        // tensor-memory base address (lane 0, first column)
-    uint32_t ncols;       // allocated columns: accumulators hh, hl, lh of 16 columns per M-tile
+    uint32_t ncols;       // allocated columns: accumulators P1V1, P1V2, P2V1 of 16 columns per M-tile
     const float *ptc;     // pre-laid-out P of the run (global)
-    int mt, ks, vr, units, npos;
+    int mt, ks, units, npos;
     int *fail;            // shared failure flag
 };
 
-// Accumulator column of product k (0: P_hi v_hi, 1: P_hi v_lo, 2: P_lo v_hi) of M-tile m.
+// Accumulator column of product k (0: P1 V1, 1: P1 V2, 2: P2 V1) of M-tile m.
 __device__ __forceinline__ uint32_t acc_col(const State &T, int k, int m)
 {
     return static_cast<uint32_t>((k * T.mt + m) * WALKERS);
@@ -273,7 +279,6 @@ __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, 
         T.ptc = ptc;
         T.mt = pl.mt;
         T.ks = pl.ks;
-        T.vr = pl.vr;
         T.units = pl.units;
         T.npos = pl.npos;
         T.fail = fail_flag;
@@ -341,10 +346,9 @@ template <int MT>
 __device__ inline void issue_mmas(const State &T, Pipe &pp)
 {
     constexpr int UNITS = static_cast<int>(STAGE_BYTES / (4096u * MT));  // halves per stage
-    constexpr int NPOS = 2 * (16 * MT) / UNITS;                            // stages per contraction
-    constexpr int VR = vgroup(128 * MT);
-    constexpr uint32_t ACC_HL = MT * WALKERS, ACC_LH = 2 * MT * WALKERS;
-    const uint32_t idesc = instr_desc_tf32(128, WALKERS);
+    constexpr int NPOS = 2 * (8 * MT) / UNITS;                             // stages per contraction
+    constexpr uint32_t ACC_12 = MT * WALKERS, ACC_21 = 2 * MT * WALKERS;
+    const uint32_t idesc = instr_desc_f16(128, WALKERS);
     const uint32_t tmem = T.tmem;
     uint64_t *const full = T.full, *const empty = T.empty;
     const uint64_t d0 = smem_desc(0, 128, 256);
@@ -361,21 +365,21 @@ __device__ inline void issue_mmas(const State &T, Pipe &pp)
         const uint32_t sa = st0 + static_cast<uint32_t>(s) * (STAGE_BYTES >> 4);
 #pragma unroll
         for (int u = 0; u < UNITS; ++u) {
-            const int q = i * UNITS + u;  // half: K-step q / 2, P_lo if q odd
+            const int q = i * UNITS + u;  // half: K-step q / 2, P2 if q odd
             const int j = q >> 1;
-            const uint32_t vj = vpos(j, VR) >> 4;
+            const uint32_t vj = vpos(j) >> 4;
             const uint32_t acc = j > 0 ? 1u : 0u;
             const uint64_t bh = d0 + vhi + vj;
             const uint64_t a0 = d0 + sa + static_cast<uint32_t>(u * MT) * 256u;
             if ((u & 1) == 0) {  // UNITS is even: the parity of q is that of u
                 const uint64_t bl = d0 + vlo + vj;
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_tf32(tmem + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
+                for (int m = 0; m < MT; ++m) mma_f16(tmem + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_tf32(tmem + ACC_HL + m * WALKERS, a0 + 256u * m, bl, idesc, acc);
+                for (int m = 0; m < MT; ++m) mma_f16(tmem + ACC_12 + m * WALKERS, a0 + 256u * m, bl, idesc, acc);
             } else {
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_tf32(tmem + ACC_LH + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
+                for (int m = 0; m < MT; ++m) mma_f16(tmem + ACC_21 + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
             }
         }
         mma_commit(empty + s);
@@ -401,36 +405,38 @@ __device__ inline void refill_stage(const State &T, Pipe &pp, int w)
             return;
         }
         pp.empty_par ^= 1u;
-        fill(T, w, idx < T.npos ? idx : idx - T.npos);
+        fill(T, w, idx % T.npos);  // npos may be below STAGES (d_pad 128): one block ahead or more
     }
 }
 
 // y = P v for the 16 walkers of the CTA (lane l of warp n holds components l E ..
-// l E + E - 1 of walker n).  Every thread of the CTA calls it (barriers inside).
+// l E + E - 1 of walker n).  sv is the power of two s_v that scales v before the split
+// and tinv = 1 / (s_p s_v).  Every thread of the CTA calls it (barriers inside).
 // Returns false if a wait gave up (y is then undefined).
 template <int E>
-__device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], int d_pad, float (&y)[E])
+__device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], int d_pad, float sv, float tinv,
+                                float (&y)[E])
 {
     static_assert(E % 4 == 0, "quads of columns");
     static_assert(STAGES + 1 <= WALKERS, "a producer warp per stage besides the issuing warp");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // B operand: the quad (walker n, columns c .. c + 3) is row n % 8 of core matrix
-    // (c % 8) / 4 of walker group n / 8 in K-step c / 8
+    // B operand: columns c .. c + 3 of walker n (8 bytes of FP16) lie in row n % 8 of
+    // core matrix (c % 16) / 8 of walker group n / 8 in K-step c / 16, at byte 2 (c % 8)
     char *vh = reinterpret_cast<char *>(T.vhi), *vl = reinterpret_cast<char *>(T.vlo);
     const uint32_t row_off = static_cast<uint32_t>((warp >> 3) * 256 + (warp & 7) * 16);
 #pragma unroll
     for (int q = 0; q < E / 4; ++q) {
         const int c = lane * E + 4 * q;
-        const uint32_t off = vpos(c >> 3, T.vr) + row_off + static_cast<uint32_t>(((c >> 2) & 1) * 128);
+        const uint32_t off = vpos(c >> 4) + row_off + static_cast<uint32_t>(((c >> 3) & 1) * 128 + (c & 7) * 2);
         float h[4], l[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const uint32_t hi = to_tf32(v[4 * q + i]);
-            h[i] = __uint_as_float(hi);
-            l[i] = __uint_as_float(to_tf32(v[4 * q + i] - h[i]));
+            const float t = v[4 * q + i] * sv;
+            h[i] = __half2float(__float2half_rn(t));
+            l[i] = (t - h[i]) * 2048.f;  // exact: t - h[i] is representable
         }
-        *reinterpret_cast<float4 *>(vh + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4 *>(vl + off) = make_float4(l[0], l[1], l[2], l[3]);
+        *reinterpret_cast<uint2 *>(vh + off) = make_uint2(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]));
+        *reinterpret_cast<uint2 *>(vl + off) = make_uint2(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]));
     }
     fence_async_smem();
     __syncthreads();
@@ -440,7 +446,7 @@ __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], i
         if (lane == 0) {
             if (warp == 0) {
                 fence_after_sync();
-                issue_mmas<E / 4>(T, pp);
+                issue_mmas<E / 4>(T, pp);  // d_pad = 32 E = 128 (E / 4) rows
             } else {
                 refill_stage(T, pp, warp - 1);
             }
@@ -452,19 +458,20 @@ __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], i
     const bool ok = !failed(T) && mbar_wait(T.done, pp.phase);
     pp.phase ^= 1u;
     fence_after_sync();
-    // Y^T[walker][d_pad] over the B operand (free once the MMAs are done), each walker's
-    // row in the lane-row layout so that the walker reads it back in quads
+    // Y^T[walker][d_pad] over the B operands (free once the MMAs are done; 2 vbytes >=
+    // 64 d_pad bytes), each walker's row in the lane-row layout so that the walker reads
+    // it back in quads
     float *ybuf = T.vhi;
     if (ok && warp < 4 * T.mt) {
         const int m = warp >> 2, q = warp & 3;
         const uint32_t lanes = static_cast<uint32_t>(32 * q) << 16;
-        float hh[16], hl[16], lh[16];
-        tmem_load16(T.tmem + lanes + acc_col(T, 0, m), hh);
-        tmem_load16(T.tmem + lanes + acc_col(T, 1, m), hl);
-        tmem_load16(T.tmem + lanes + acc_col(T, 2, m), lh);
+        float a11[16], a12[16], a21[16];
+        tmem_load16(T.tmem + lanes + acc_col(T, 0, m), a11);
+        tmem_load16(T.tmem + lanes + acc_col(T, 1, m), a12);
+        tmem_load16(T.tmem + lanes + acc_col(T, 2, m), a21);
         const int row = swz_col<E>(m * 128 + 32 * q + lane);
 #pragma unroll
-        for (int n = 0; n < WALKERS; ++n) ybuf[n * d_pad + row] = hh[n] + (hl[n] + lh[n]);
+        for (int n = 0; n < WALKERS; ++n) ybuf[n * d_pad + row] = fmaf(a12[n] + a21[n], 0x1p-11f, a11[n]) * tinv;
     }
     fence_before_sync();
     __syncthreads();

@@ -599,8 +599,8 @@ def test_cooperative_dense_walk_equals_per_walker_walk():
 @pytest.mark.parametrize("kind,d,n,steps", [("dense", 128, 32, 20), ("dense_mix", 256, 32, 12),
                                             ("dense_mix", 512, 24, 10), ("dense", 512, 17, 12)])
 def test_tensor_core_dense_trajectories_match_oracle(kind, d, n, steps):
-    """The dense walk with the contraction y = P v on the tensor cores (tcgen05, 3xTF32, accumulators
-    in tensor memory): at most 20 steps from identical FP32 inputs give the same inside/outside
+    """The dense walk with the contraction y = P v on the tensor cores (tcgen05 kind::f16 on the
+    scaled two-term FP16 split of P and v, accumulators in tensor memory): at most 20 steps from identical FP32 inputs give the same inside/outside
     decisions, step counts and reservoir picks as the FP64 oracle, and outputs within 1e-5
     (d_pad 128, 256, 512; a ragged last CTA of walkers)."""
     w = W.small_workload(kind, d, 2 * n, seed=17)
