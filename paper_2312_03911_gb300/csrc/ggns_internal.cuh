@@ -86,7 +86,7 @@ struct RunDesc {
 //   lo[d_pad], hi[d_pad], means[n_comp][d_pad], comp_a[n_comp], comp_b[n_comp],
 //   precision[d][d_pad] (dense kinds), pmu[n_comp][d_pad] (dense mixture: P mu_k).
 // comp_a/comp_b: ISO kinds: a = 1/sigma^2, b = log w_k - d/2 log(2 pi sigma^2);
-//                dense kinds: a unused, b = log w_k - mu_k^T P mu_k / 2 (mixture).
+//                dense kinds: a unused, b = log w_k (mixture), 0 (single Gaussian).
 struct ParLayout {
     long lo, hi, means, comp_a, comp_b, prec, pmu, ptc, total;
 };

@@ -580,11 +580,94 @@ __device__ __forceinline__ void row_store(float *dst, const float (&v)[E])
     }
 }
 
+// The dense mixture after y = P x on the tensor-core walk (one walker per warp, means
+// and P mu in the lane-row layout), for up to 8 components: the quadratic forms
+// q_k = (x - mu_k).(y - P mu_k) of all components, their warp sums interleaved level by
+// level (eight independent chains instead of one after another), then the log-sum-exp.
+// Returns log L and, in r_lane, the responsibility r_k of component k = lane % 8; the
+// score g = -(y - sum_k r_k P mu_k) (the r_k sum to one) is formed by mix_score8 only
+// where a reflection needs it.
+template <int E>
+__device__ __forceinline__ float dense_mix_finish8(const RunDesc &D, const ParView &P, const float (&x)[E],
+                                                   const float (&y)[E], float &r_lane)
+{
+    constexpr int KC = 8;
+    const int K = D.n_comp;
+    const int dp = D.d_pad;
+    const int lane = threadIdx.x & 31;
+    float q[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        q[k] = 0.f;
+        if (k < K) {
+            const float *mu = P.means + (long)k * dp;
+            const float *pm = P.pmu + (long)k * dp;
+#pragma unroll
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 a = lane_quad<E>(mu, lane, h), b = lane_quad<E>(pm, lane, h);
+                q[k] = fmaf(x[4 * h] - a.x, y[4 * h] - b.x, q[k]);
+                q[k] = fmaf(x[4 * h + 1] - a.y, y[4 * h + 1] - b.y, q[k]);
+                q[k] = fmaf(x[4 * h + 2] - a.z, y[4 * h + 2] - b.z, q[k]);
+                q[k] = fmaf(x[4 * h + 3] - a.w, y[4 * h + 3] - b.w, q[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < KC; ++k) q[k] += __shfl_xor_sync(0xffffffffu, q[k], o);
+    }
+    float m = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        q[k] = (k < K) ? P.b[k] - 0.5f * q[k] : -INFINITY;  // t_k
+        m = fmaxf(m, q[k]);
+    }
+    float s = 0.f, w_lane = 0.f;
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+        const float w = (k < K) ? expf(q[k] - m) : 0.f;  // w_k
+        s += w;
+        if ((lane & 7) == k) w_lane = w;
+    }
+    r_lane = w_lane / s;
+    return D.lik_const + m + logf(s);
+}
+
+// The score of the dense mixture from y (held in g) and the responsibilities (r_k in
+// lane k of every eight): g = -y + sum_k r_k P mu_k.
+template <int E>
+__device__ __forceinline__ void mix_score8(const RunDesc &D, const ParView &P, float r_lane, float (&g)[E])
+{
+    const int K = D.n_comp;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = -g[e];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float rk = __shfl_sync(0xffffffffu, r_lane, k);
+        if (k < K) {
+            const float *pm = P.pmu + (long)k * D.d_pad;
+#pragma unroll
+            for (int h = 0; h < E / 4; ++h) {
+                const float4 b = lane_quad<E>(pm, lane, h);
+                g[4 * h] = fmaf(rk, b.x, g[4 * h]);
+                g[4 * h + 1] = fmaf(rk, b.y, g[4 * h + 1]);
+                g[4 * h + 2] = fmaf(rk, b.z, g[4 * h + 2]);
+                g[4 * h + 3] = fmaf(rk, b.w, g[4 * h + 3]);
+            }
+        }
+    }
+}
+
 // Dense likelihood of the 16 walkers of a CTA with the contraction on the tensor cores
 // (ggns_tc.cuh); every thread of the CTA calls it.  `ok` turns false if a wait gave up.
+// lazy: for the mixture of up to 8 components g holds y and r_lane the responsibilities
+// on return, and mix_score8 forms the score when a reflection needs it; otherwise g is
+// the score.
 template <int KIND, int E>
 __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
-                              const tc::State &T, tc::Pipe &pp, bool &ok)
+                              const tc::State &T, tc::Pipe &pp, bool &ok, float &r_lane, bool &lazy)
 {
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
     // v is staged in g (the score is written only after the contraction)
@@ -597,6 +680,14 @@ __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&
         for (int i = 0; i < 4; ++i) {
             const int e = 4 * h + i;
             g[e] = (c0 + e < D.d) ? x[e] - m4[i] : 0.f;
+        }
+    }
+    lazy = false;
+    if constexpr (KIND == NS_LIK_DENSE_MIX) {
+        if (D.n_comp <= 8) {
+            ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, g);  // v is read before y is written
+            lazy = true;
+            return dense_mix_finish8<E>(D, P, x, g, r_lane);
         }
     }
     float y[E];
@@ -1034,6 +1125,8 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     __shared__ tc::State T;
     tc::Pipe tc_pipe;
     bool tc_ok = true;
+    float tc_r = 0.f;      // responsibility of component lane % 8 (tensor-core mixture walk)
+    bool tc_lazy = false;  // g holds y until the score is needed
     if constexpr (TC) {
         // a CTA without walkers of this run leaves before it takes tensor memory
         if (static_cast<long>(blockIdx.x) * (blockDim.x / 32) >= W) return;
@@ -1166,7 +1259,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         const bool lfold = fold_box<KIND, E, COOP>(D, P, x, p, c0);
         float ll;
         if constexpr (TC) {
-            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok);
+            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok, tc_r, tc_lazy);
         } else if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
         } else {
@@ -1199,18 +1292,30 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
                 pnb = fmaf(p[e], nb, pnb);
             }
         }
+        // the score enters only a reflection off the iso-likelihood contour; the tensor-core
+        // walk (one walker per warp: the test is uniform over the warp) skips it on the
+        // other steps
+        bool need_g = true;
+        if constexpr (TC) {
+            need_g = !(ll > lstar);
+            if (need_g && tc_lazy) mix_score8<E>(D, P, tc_r, g);
+        }
+        if (need_g) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            pg = fmaf(p[e], g[e], pg);
-            gg = fmaf(g[e], g[e], gg);
+            for (int e = 0; e < E; ++e) {
+                pg = fmaf(p[e], g[e], pg);
+                gg = fmaf(g[e], g[e], gg);
+            }
         }
         // the box count and the fold flag (bit 16) in one group sum
         outbox = gsum_i<G>(outbox | (lfold ? 0x10000 : 0));
         const bool folded = (outbox >> 16) != 0;
         outbox &= 0xffff;
         pnb = gsum<G>(pnb);
-        pg = gsum<G>(pg);
-        gg = gsum<G>(gg);
+        if (need_g) {
+            pg = gsum<G>(pg);
+            gg = gsum<G>(gg);
+        }
         const bool outside = (outbox > 0) || !(ll > lstar);
         if (stepping && outside) {
             if (outbox > 0) {

@@ -9,11 +9,13 @@
 // core-matrix order when the context is created, streams from global memory through
 // a ring of STAGES shared-memory stages of 32 KB (a stage holds P1 and P2 of one
 // K-step of 16 columns for every 128-row M-tile, or of several K-steps when d_pad is
-// small).  Lane 0 of warp 0 issues, per half, the MMAs of the products P1 V1,
-// P1 V2 and P2 V1 (kind::f16, M = 128, N = 16, K = 16, FP32 accumulation in tensor
-// memory: the three products in accumulators of their own, so that an MMA never
-// waits for the one issued just before it) and commits each stage's MMAs to that
-// stage's `empty` barrier.  The read-back forms
+// small).  V1 and V2 form one B operand of 32 rows per K-step, so lane 0 of warp 0
+// issues, per K-step and 128-row tile, two MMAs (kind::f16, K = 16, FP32 accumulation
+// in tensor memory): P1 [V1 | V2] with N = 32 and P2 V1 with N = 16, each into an
+// accumulator of its own (an MMA never waits for the one issued just before it; at
+// these widths an MMA costs about the same time whatever its N, so the merge saves a
+// third of the tensor time), and commits each stage's MMAs to that stage's `empty`
+// barrier.  The read-back forms
 //     y = (P1 V1 + 2^-11 (P1 V2 + P2 V1)) / (s_p s_v),
 // whose neglected term 2^-22 P2 V2 and the split's rounding leave y within about
 // 2^-22 of |P| |v| (each factor carries 22 significant bits; the scales keep every
@@ -191,18 +193,19 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// The B operand of K-step j (its 16 walkers x 16 FP16 columns, 512 bytes) starts at
-// byte vpos(j) of V1 / V2: one extra 16 bytes after every K-step puts the 16-byte
-// rows that the lanes of a quarter-warp write (a lane's E columns lie in K-step
-// lane E / 16) into distinct bank groups.
-__host__ __device__ constexpr uint32_t vpos(int j) { return 528u * j; }
+// The B operand of K-step j starts at byte vpos(j): 32 rows of 16 FP16 columns in four
+// groups of 8 rows (256 bytes apart), rows 0-15 the walkers' V1 and rows 16-31 their
+// V2 (V2 of walker n is row 16 + n, 512 bytes after its V1), 1 KB per K-step; one
+// extra 16 bytes after every K-step puts the rows that the lanes of a quarter-warp
+// write (a lane's E columns lie in K-step lane E / 16) into distinct bank groups.
+__host__ __device__ constexpr uint32_t vpos(int j) { return 1040u * j; }
 
 // Layout of the tensor-core state in dynamic shared memory (bytes from a 1024-aligned base).
 struct Plan {
     int mt, ks;              // 128-row M-tiles, 16-column K-steps of d_pad
     int units;               // halves (P_hi or P_lo of one K-step, mt x 4 KB) per stage
     int npos;                // stages consumed by one contraction (2 ks / units)
-    uint32_t vbytes;         // one B operand (V1 or V2)
+    uint32_t vbytes;         // the B operands (V1 and V2 of every K-step)
     uint32_t v_off, stage_off, bar_off, total;
 };
 
@@ -214,8 +217,8 @@ __host__ __device__ inline Plan plan(int d_pad)
     p.units = static_cast<int>(STAGE_BYTES / (4096u * p.mt));
     p.npos = 2 * p.ks / p.units;
     p.vbytes = (vpos(p.ks) + 127u) & ~127u;
-    p.v_off = 0;                                            // V1 then V2
-    p.stage_off = p.v_off + 2 * p.vbytes;
+    p.v_off = 0;
+    p.stage_off = p.v_off + p.vbytes;
     p.bar_off = p.stage_off + STAGES * STAGE_BYTES;         // full[S], empty[S], done, tmem base
     p.total = p.bar_off + (2 * STAGES + 1) * 8 + 16;
     return p;
@@ -227,7 +230,7 @@ __host__ __device__ inline long ptc_floats(int d_pad) { return 1l * d_pad * d_pa
 // Per-CTA state (shared-memory pointers, tensor-memory base), kept in shared memory:
 // thread 0 writes it, every thread reads it.
 struct State {
-    float *vhi, *vlo;     // B operands V1 and V2 (Y^T aliases both after the MMAs)
+    float *vb;            // B operands (Y^T aliases them after the MMAs)
     char *stages;
     uint64_t *full, *empty, *done;
     uint32_t *tmem_slot;
@@ -238,10 +241,11 @@ struct State {
     int *fail;            // shared failure flag
 };
 
-// Accumulator column of product k (0: P1 V1, 1: P1 V2, 2: P2 V1) of M-tile m.
+// Accumulator column of product k (0: P1 V1, 1: P1 V2, 2: P2 V1) of M-tile m: the N = 32
+// accumulator of P1 [V1 | V2] of tile m at 32 m, that of P2 V1 at 32 mt + 16 m.
 __device__ __forceinline__ uint32_t acc_col(const State &T, int k, int m)
 {
-    return static_cast<uint32_t>((k * T.mt + m) * WALKERS);
+    return static_cast<uint32_t>(k < 2 ? 2 * WALKERS * m + k * WALKERS : 2 * WALKERS * T.mt + WALKERS * m);
 }
 
 // Each thread's view of the pipeline (32-bit counters, advanced incrementally): the
@@ -269,8 +273,7 @@ __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, 
 {
     if (threadIdx.x == 0) {
         const Plan pl = plan(d_pad);
-        T.vhi = reinterpret_cast<float *>(base + pl.v_off);
-        T.vlo = reinterpret_cast<float *>(base + pl.v_off + pl.vbytes);
+        T.vb = reinterpret_cast<float *>(base + pl.v_off);
         T.stages = base + pl.stage_off;
         T.full = reinterpret_cast<uint64_t *>(base + pl.bar_off);
         T.empty = T.full + STAGES;
@@ -347,12 +350,12 @@ __device__ inline void issue_mmas(const State &T, Pipe &pp)
 {
     constexpr int UNITS = static_cast<int>(STAGE_BYTES / (4096u * MT));  // halves per stage
     constexpr int NPOS = 2 * (8 * MT) / UNITS;                             // stages per contraction
-    constexpr uint32_t ACC_12 = MT * WALKERS, ACC_21 = 2 * MT * WALKERS;
-    const uint32_t idesc = instr_desc_f16(128, WALKERS);
+    constexpr uint32_t ACC_2 = 2 * MT * WALKERS;  // P2 V1 accumulators (after the N = 32 ones)
+    const uint32_t idesc32 = instr_desc_f16(128, 2 * WALKERS), idesc16 = instr_desc_f16(128, WALKERS);
     const uint32_t tmem = T.tmem;
     uint64_t *const full = T.full, *const empty = T.empty;
     const uint64_t d0 = smem_desc(0, 128, 256);
-    const uint32_t vhi = smem_addr(T.vhi) >> 4, vlo = smem_addr(T.vlo) >> 4, st0 = smem_addr(T.stages) >> 4;
+    const uint32_t vb = smem_addr(T.vb) >> 4, st0 = smem_addr(T.stages) >> 4;
     int s = pp.s0;
     uint32_t par = pp.full_par;
 #pragma unroll 1
@@ -369,17 +372,14 @@ __device__ inline void issue_mmas(const State &T, Pipe &pp)
             const int j = q >> 1;
             const uint32_t vj = vpos(j) >> 4;
             const uint32_t acc = j > 0 ? 1u : 0u;
-            const uint64_t bh = d0 + vhi + vj;
+            const uint64_t b = d0 + vb + vj;  // rows 0-15 (V1), or 0-31 (V1 and V2) with N = 32
             const uint64_t a0 = d0 + sa + static_cast<uint32_t>(u * MT) * 256u;
             if ((u & 1) == 0) {  // UNITS is even: the parity of q is that of u
-                const uint64_t bl = d0 + vlo + vj;
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_f16(tmem + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
-#pragma unroll
-                for (int m = 0; m < MT; ++m) mma_f16(tmem + ACC_12 + m * WALKERS, a0 + 256u * m, bl, idesc, acc);
+                for (int m = 0; m < MT; ++m) mma_f16(tmem + 2 * WALKERS * m, a0 + 256u * m, b, idesc32, acc);
             } else {
 #pragma unroll
-                for (int m = 0; m < MT; ++m) mma_f16(tmem + ACC_21 + m * WALKERS, a0 + 256u * m, bh, idesc, acc);
+                for (int m = 0; m < MT; ++m) mma_f16(tmem + ACC_2 + m * WALKERS, a0 + 256u * m, b, idesc16, acc);
             }
         }
         mma_commit(empty + s);
@@ -422,7 +422,7 @@ __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], i
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // B operand: columns c .. c + 3 of walker n (8 bytes of FP16) lie in row n % 8 of
     // core matrix (c % 16) / 8 of walker group n / 8 in K-step c / 16, at byte 2 (c % 8)
-    char *vh = reinterpret_cast<char *>(T.vhi), *vl = reinterpret_cast<char *>(T.vlo);
+    char *vh = reinterpret_cast<char *>(T.vb), *vl = vh + 512;  // V2 of walker n is row 16 + n
     const uint32_t row_off = static_cast<uint32_t>((warp >> 3) * 256 + (warp & 7) * 16);
 #pragma unroll
     for (int q = 0; q < E / 4; ++q) {
@@ -458,10 +458,10 @@ __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], i
     const bool ok = !failed(T) && mbar_wait(T.done, pp.phase);
     pp.phase ^= 1u;
     fence_after_sync();
-    // Y^T[walker][d_pad] over the B operands (free once the MMAs are done; 2 vbytes >=
-    // 64 d_pad bytes), each walker's row in the lane-row layout so that the walker reads
+    // Y^T[walker][d_pad] over the B operands (free once the MMAs are done; vbytes >=
+    // 65 d_pad bytes), each walker's row in the lane-row layout so that the walker reads
     // it back in quads
-    float *ybuf = T.vhi;
+    float *ybuf = T.vb;
     if (ok && warp < 4 * T.mt) {
         const int m = warp >> 2, q = warp & 3;
         const uint32_t lanes = static_cast<uint32_t>(32 * q) << 16;
