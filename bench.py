@@ -13,6 +13,7 @@ the replicas' mean is within 0.2 nats of the closed form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ggns|reference]
                   [--workload c5|c2]
+  python bench.py --profile-case [--workload c5|c2] [--iters N] [--n-steps S]   (ncu captures)
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own runs
 (independent runs: no collective on the data path, weak scaling).
@@ -44,11 +45,19 @@ C2_REPLICAS = 17
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture, valid only
-# for the kernel sources with these hashes (None: not captured for these sources).
-TRAFFIC = {"c5": None, "c2": None}
-TRAFFIC_SOURCES = {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": None,
-                   "paper_2312_03911_gb300/csrc/ggns_internal.cuh": None}
+# DRAM bytes (read + write) of the dominant kernel from one ncu capture, valid only for the kernel
+# sources with these hashes: c5 per walker point-step (the records of the steps dominate, so the
+# traffic of a launch grows with the point-steps it takes; scaled to the timed launches' mean),
+# c2 per launch (one launch of the timed batch).
+TRAFFIC = {
+    "c5": {"bytes_per_point_step": 1663.59,
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "f41d3e69d9233436",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "6e93cfbb66cf0153",
+                       "paper_2312_03911_gb300/csrc/ggns_tc.cuh": "c425a27c121efb13"}},
+    "c2": {"bytes_per_launch": 83.198208e6,
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "f41d3e69d9233436",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "6e93cfbb66cf0153"}},
+}
 
 
 def lane_ops_per_point_step(d: int, K: int, out_frac: float, rng: bool = True) -> float:
@@ -154,17 +163,21 @@ def sum_over_ranks(x: float, dist, device: str) -> float:
     return float(tt.item())
 
 
-def measured_traffic(name: str):
-    """The profiled DRAM traffic per launch of the workload's dominant kernel, or None when it
-    was not captured for the current kernel sources."""
+def measured_traffic(name: str, point_steps_per_launch: float):
+    """The profiled DRAM traffic of one launch of the workload's dominant kernel (c5: scaled to
+    the mean point-steps of the timed launches), or None when it was not captured for the
+    current kernel sources."""
     import hashlib
-    if TRAFFIC.get(name) is None:
+    t = TRAFFIC.get(name)
+    if not t or not t["sources"]:
         return None
-    for rel, h in TRAFFIC_SOURCES.items():
+    for rel, h in t["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
-            if h is None or hashlib.sha256(f.read()).hexdigest()[:16] != h:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != h:
                 return None
-    return TRAFFIC[name]
+    if "bytes_per_point_step" in t:
+        return t["bytes_per_point_step"] * point_steps_per_launch if t["bytes_per_point_step"] else None
+    return t["bytes_per_launch"]
 
 
 def load_peaks():
@@ -298,7 +311,29 @@ def _timed_steps(s, R, steps, stream, flush, dist, seed0, grad=True):
     return times, pts, logz, errs
 
 
-def _c2_time_to_logz(ggns, torch, stream, flush, rank, warmup):
+def _c2_throughput(ggns, stream, flush, rank, reps, f_sm):
+    """Throughput mode of the c2 walk: reps seeded replicas in one batch (more walkers than the
+    GPU holds at once), one warm-up batch and one timed batch; the walker kernel's lane-op rate
+    against the ALU peak at the sampled SM clock."""
+    w, runs = runs_of("c2", reps, rank)
+    s = ggns.Sampler(runs, stream=stream.cuda_stream)
+    s.restart(W.SEED_BASE + 5000)
+    s.run()
+    s.profile(reset=True)
+    times, pts, _, _ = _timed_steps(s, reps, 1, stream, flush, None, W.SEED_BASE + 6000, grad=False)
+    prof = s.profile(reset=True)
+    s.close()
+    ops = lane_ops_per_point_step(32, 4, 0.12, rng=not prof.get("noise_steps", 0) > 0)
+    hss_s = prof["hss_ms"] / 1000.0
+    ach = ops * sum(pts) / hss_s if hss_s > 0 else None
+    peak = SMS * FP32_LANES_PER_SM * f_sm
+    return {"replicas": reps, "point_steps_per_s": sum(pts) / sum(times), "ms_per_batch": 1000.0 * sum(times),
+            "hss_achieved": ach / 1e12 if ach else None, "hss_peak": peak / 1e12, "unit": "Tlane-op/s",
+            "hss_frac": ach / peak if ach else None,
+            "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times))}
+
+
+def _c2_time_to_logz(ggns, torch, stream, flush, rank, warmup, f_sm):
     """c2x17 in one batch: time to a mean log Z of the 17 replicas, against the plain path."""
     w, runs = runs_of("c2", C2_REPLICAS, rank)
     s = ggns.Sampler(runs, stream=stream.cuda_stream)
@@ -345,8 +380,11 @@ def _c2_time_to_logz(ggns, torch, stream, flush, rank, warmup):
                               "host-synchronised launch chain per iteration (no graph, no batching), CUDA events",
                       "speedup": plain_ms / ms},
             "hss_roofline": {"bound": "alu", "achieved": ops * sum(pts) / hss_s / 1e12 if hss_s > 0 else None,
+                             "peak": SMS * FP32_LANES_PER_SM * f_sm / 1e12,
+                             "frac": ops * sum(pts) / hss_s / (SMS * FP32_LANES_PER_SM * f_sm) if hss_s > 0 else None,
                              "unit": "Tlane-op/s", "ops_per_point_step": ops,
-                             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times))}}
+                             "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times))},
+            "throughput_mode": _c2_throughput(ggns, stream, flush, rank, 8 * C2_REPLICAS, f_sm)}
 
 
 def gpu_arm(args):
@@ -405,7 +443,8 @@ def gpu_arm(args):
             peak = SMS * FP32_LANES_PER_SM * 2.0 * f_sm
             bound, pnote = "alu", f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {f_sm / 1e6:.0f} MHz"
         roof = {"bound": bound, "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": measured_traffic(name),
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": measured_traffic(name, sum(pts) / max(prof["hss_iters"], 1)),
                 "kernel": "dense-mixture HSS walk (k_hss1, CTA-cooperative)", "flops_per_point_step": flops,
                 "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
                 "hss_ms_per_iteration": prof["hss_ms_sum"] / max(prof["hss_iters"], 1), "peak_note": pnote}
@@ -415,7 +454,7 @@ def gpu_arm(args):
         peak = SMS * FP32_LANES_PER_SM * f_sm
         roof = {"bound": "alu", "achieved": achieved / 1e12 if achieved else None, "peak": peak / 1e12,
                 "unit": "Tlane-op/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": measured_traffic(name), "kernel": "k_hss1 + k_hss_pick", "ops_per_point_step": ops,
+                "traffic": measured_traffic(name, 0.0), "kernel": "k_hss1 + k_hss_pick", "ops_per_point_step": ops,
                 "hss_busy_fraction_of_step": prof["hss_ms"] / (1000.0 * sum(times)),
                 "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} lanes x median SM clock {f_sm / 1e6:.0f} MHz"}
     # e2e: through the C ABI from host buffers: create (H2D of the problem), run, results and the
@@ -440,7 +479,7 @@ def gpu_arm(args):
     e2e_value = pts[-1] / (sum(e2e_t) / len(e2e_t))
     c2leg = None
     if name == "c5" and world == 1 and not args.no_c2:
-        c2leg = _c2_time_to_logz(ggns, torch, stream, flush, rank, args.warmup)
+        c2leg = _c2_time_to_logz(ggns, torch, stream, flush, rank, args.warmup, f_sm)
     line = None
     if rank == 0:
         cpu = None
@@ -478,6 +517,36 @@ def gpu_arm(args):
     return 0
 
 
+def profile_case(args):
+    """A bounded case for ncu captures (not a benchmark line): one run of the workload with the
+    HSS step cap lowered to --n-steps (so the step records stay small) stepped --iters
+    iterations through ns_step."""
+    import torch
+    from paper_2312_03911_gb300 import build as B
+    from paper_2312_03911_gb300 import ggns
+    torch.cuda.set_device(0)
+    B.build()
+    ggns.load()
+    w = W.workload(args.workload, n_steps=args.n_steps)
+    s = ggns.Sampler([w])
+    # one iteration per ns_step: iteration i launches the walker kernel once, so the
+    # point-steps of launch i are the growth of n_like over iteration i
+    steps, last = [], s.result(0, check=False)["n_like"]
+    for _ in range(args.iters):
+        done = s.step(1)
+        nl = s.result(0, check=False)["n_like"]
+        steps.append(nl - last)
+        last = nl
+        if done:
+            break
+    torch.cuda.synchronize()
+    r = s.result(0, check=False)
+    print(json.dumps({"profile_case": args.workload, "n_steps": args.n_steps, "n_iter": r["n_iter"],
+                      "n_like": r["n_like"], "status": r["status"], "point_steps_per_iteration": steps}), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,7 +556,13 @@ def main():
     ap.add_argument("--workload", default="c5", choices=["c5", "c2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c2", action="store_true", help="skip the c2x17 time-to-log-Z leg")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run a bounded case for ncu captures instead of the benchmark (see --iters, --n-steps)")
+    ap.add_argument("--iters", type=int, default=100, help="--profile-case: iterations to step")
+    ap.add_argument("--n-steps", type=int, default=200, help="--profile-case: HSS step cap")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return reference_arm(args)
     return gpu_arm(args)

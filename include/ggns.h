@@ -43,7 +43,9 @@ typedef enum {
     NS_ERR_STUCK = 5,    /* reserved: walkers could not leave an empty slice            */
     NS_ERR_NUMERIC = 6,  /* no live point has a finite log-likelihood                   */
     NS_ERR_NOT_DONE = 7, /* the run stopped at max_iters before its termination test    */
-    NS_ERR_CAPACITY = 8  /* dead-point arena, cluster table or output buffer too small  */
+    NS_ERR_CAPACITY = 8, /* dead-point arena, cluster table or output buffer too small  */
+    NS_ERR_BOUNDS = 9    /* checked builds only (GGNS_CHECKED): an index check of the   */
+                         /* dead-point arena, the step records or the live slots failed */
 } ns_status;
 
 typedef enum {

@@ -161,6 +161,22 @@ struct RunState {
     long n_fold;           // inside steps on which the box reflected the walker (box_fold)
 };
 
+// Checked builds (compiled with -DGGNS_CHECKED, the stand-in for a memory checker):
+// indexes into the dead-point arena, the step records and the live slots are checked
+// before the access; a failed check skips the access and leaves NS_ERR_BOUNDS in the
+// run's status, which the host reports like any other status.  In the default build
+// the check is the constant true.
+#ifdef GGNS_CHECKED
+__device__ __forceinline__ bool gg_in(long i, long n, RunState *S)
+{
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&S->status, 0, static_cast<int>(NS_ERR_BOUNDS));
+    return false;
+}
+#else
+__device__ __forceinline__ bool gg_in(long, long, RunState *) { return true; }
+#endif
+
 // FP64 cluster statistics of one run (Appendix H), log space.
 struct Stats {
     double logZp[CMAX], logZp2[CMAX], logZXp[CMAX], logZpXp[CMAX], logXp[CMAX], logXp2[CMAX];

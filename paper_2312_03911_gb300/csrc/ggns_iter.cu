@@ -508,6 +508,7 @@ __device__ void final_sweep_body(DevCtx C, int r)
     };
     // dead records: log L, log prior mass, label, x
     for (int j = tid; j < k; j += blockDim.x) {
+        if (!gg_in(dbase + j - D.dead_off, D.dead_cap, S)) continue;
         D.dead_logl[dbase + j] = (float)kL[j];
         D.dead_logw[dbase + j] = E->logw[kP[j]];
         D.dead_label[dbase + j] = kP[j];
@@ -579,8 +580,10 @@ __device__ void sort_body(DevCtx C, int r, unsigned char *sraw)
     for (int j = tid; j < k; j += blockDim.x) {
         const int s0 = (int)(keys[j] & 0xffffffffu);
         const int c = label[s0];
-        D.dead_logl[dbase + j] = logl[s0];
-        D.dead_label[dbase + j] = c;
+        if (gg_in(dbase + j, D.dead_cap, S) && gg_in(s0, D.n_live, S)) {
+            D.dead_logl[dbase + j] = logl[s0];
+            D.dead_label[dbase + j] = c;
+        }
         atomicAdd(&s_m[c], 1);
     }
     __syncthreads();
@@ -739,12 +742,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_evidence(DevCtx C, int r0)
     }
     const long dbase = S->dead_base;
     for (int j = tid; j < k; j += blockDim.x) {
-        kL[j] = (double)D.dead_logl[dbase + j];
-        kP[j] = D.dead_label[dbase + j];
+        const bool in = gg_in(dbase + j, D.dead_cap, S);
+        kL[j] = in ? (double)D.dead_logl[dbase + j] : 0.0;
+        kP[j] = in ? D.dead_label[dbase + j] : 0;
     }
     __syncthreads();
     evidence_batch(st, &S->logz, &S->logz2, k, kL, kP, E);
-    for (int j = tid; j < k; j += blockDim.x) D.dead_logw[dbase + j] = E->logw[kP[j]];
+    for (int j = tid; j < k; j += blockDim.x)
+        if (gg_in(dbase + j, D.dead_cap, S)) D.dead_logw[dbase + j] = E->logw[kP[j]];
     __syncthreads();
     if (tid < CMAX && st->alive[tid]) st->n[tid] += S->spawn_cnt[tid];
     __syncthreads();
@@ -897,6 +902,8 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
     }
     if (w >= W) return;
     const long base = rec_base[r] + (long)w * R.rec_len;
+    // the window lies inside this walker's record rows
+    if (tstop > 0 && !gg_in(tstop - 1, R.rec_len, S)) return;
     // the steps of the window that enter the reservoir: inside steps from t_save on;
     // with pick_all every step, a drawn outside step rejecting (the start point)
     int pick = 0, count = 0, nout = 0, nfold = 0;
@@ -925,6 +932,7 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
     }
     if (pick_out) pick = 0;  // rejected: the walker keeps its start point
     const int slot = C.order[D.pt_off + w];
+    if (!gg_in(slot, D.n_live, S) || !gg_in(C.start_slot[D.w_off + w], D.n_live, S)) return;
     float *dst = C.fa + D.x_off + (long)slot * dp;
     const float *src = (pick > 0) ? R.x + (base + pick - 1) * R.xs
                                   : C.fa + D.x_off + (long)C.start_slot[D.w_off + w] * dp;
@@ -945,53 +953,99 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
 // ------------------------------------------------------------------------
 // Nearest-survivor search, one query per lane: a CTA of TER_WARPS warps serves 32
 // queries (new points) held transposed in shared memory (q[c * 33 + lane], no bank
-// conflicts); warp w scans the candidates w, w + TER_WARPS, ..., each candidate row
-// read once per warp as a broadcast, so a (query, candidate) pair costs one shared
-// load, one subtraction and one fused multiply-add per coordinate.  Squared
-// distances accumulate over the coordinates in order (FP32, round to nearest), the
-// order the oracle uses; ties go to the lower candidate key.  Returns, in every
+// conflicts).  The candidate rows come through shared memory in tiles of TER_TILE
+// rows (rows padded with zeros to ds = d rounded up to 4); warp w stages and scans
+// rows w, w + TER_WARPS, ... of a tile (TER_TILE / TER_WARPS rows, their loads in
+// flight together, one accumulator each; only warp barriers) and walks the
+// coordinates four at a time: the query's four from shared memory once, each row's
+// four as one broadcast float4.  Squared
+// distances accumulate over the coordinates in order (FP32, round to nearest; the
+// zero padding adds fma(0, 0, s) = s), the order the oracle uses; ties go to the lower
+// candidate key, so the result does not depend on the scan order.  Returns, in every
 // lane of warp 0, the key of its query's nearest candidate (-1 if none).
 constexpr int TER_WARPS = 4;
+constexpr int TER_TILE = 32;
+constexpr int TER_ROWS = TER_TILE / TER_WARPS;  // rows of a tile per warp
+
+__device__ __forceinline__ void ter_take(float s, int k, float &best, int &bk)
+{
+    if (s < best || (s == best && k < bk)) {
+        best = s;
+        bk = k;
+    }
+}
+
+__host__ __device__ inline int ter_ds(int d) { return (d + 3) & ~3; }
 
 template <typename RowF, typename KeyF>
-__device__ __forceinline__ int tile_nearest(const float *q, int d, int m, RowF cand, KeyF key, float *mb, int *mk)
+__device__ __forceinline__ int tile_nearest(const float *q, int d, int m, RowF cand, KeyF key, float *mb, int *mk,
+                                            float *ct)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ds = ter_ds(d);
     float best = INFINITY;
     int bk = 0x7fffffff;
-    for (int i = warp; i < m; i += TER_WARPS) {
-        const float *row = cand(i);
-        float s = 0.f;
-        for (int c = 0; c < d; ++c) {
-            const float diff = q[c * 33 + lane] - __ldg(row + c);
-            s = __fmaf_rn(diff, diff, s);
+    for (int t0 = 0; t0 < m; t0 += TER_TILE) {
+        const int nt = min(TER_TILE, m - t0);
+        // each warp stages its own rows of the tile (rows warp + TER_WARPS j): the row
+        // addresses first, then every row's loads in flight together, coalesced over lanes
+        const float *rp[TER_ROWS];
+#pragma unroll
+        for (int j = 0; j < TER_ROWS; ++j) {
+            const int r = warp + TER_WARPS * j;
+            rp[j] = (r < nt) ? cand(t0 + r) : nullptr;
         }
-        const int k = key(i);
-        if (s < best || (s == best && k < bk)) {
-            best = s;
-            bk = k;
+        __syncwarp();  // this warp's previous rows are consumed
+        for (int c = lane; c < ds; c += 32) {
+            float v[TER_ROWS];
+#pragma unroll
+            for (int j = 0; j < TER_ROWS; ++j) v[j] = (rp[j] != nullptr && c < d) ? __ldg(rp[j] + c) : 0.f;
+#pragma unroll
+            for (int j = 0; j < TER_ROWS; ++j) ct[(warp + TER_WARPS * j) * ds + c] = v[j];
+        }
+        __syncwarp();
+        float acc[TER_ROWS];
+#pragma unroll
+        for (int j = 0; j < TER_ROWS; ++j) acc[j] = 0.f;
+        for (int c0 = 0; c0 < ds; c0 += 4) {
+            const float q0 = q[c0 * 33 + lane], q1 = q[(c0 + 1) * 33 + lane];
+            const float q2 = q[(c0 + 2) * 33 + lane], q3 = q[(c0 + 3) * 33 + lane];
+#pragma unroll
+            for (int j = 0; j < TER_ROWS; ++j) {
+                const int r = warp + TER_WARPS * j;
+                if (r < nt) {
+                    const float4 v = *reinterpret_cast<const float4 *>(ct + r * ds + c0);
+                    float df = q0 - v.x;
+                    acc[j] = __fmaf_rn(df, df, acc[j]);
+                    df = q1 - v.y;
+                    acc[j] = __fmaf_rn(df, df, acc[j]);
+                    df = q2 - v.z;
+                    acc[j] = __fmaf_rn(df, df, acc[j]);
+                    df = q3 - v.w;
+                    acc[j] = __fmaf_rn(df, df, acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TER_ROWS; ++j) {
+            const int r = warp + TER_WARPS * j;
+            if (r < nt) ter_take(acc[j], key(t0 + r), best, bk);
         }
     }
     mb[warp * 32 + lane] = best;
     mk[warp * 32 + lane] = bk;
     __syncthreads();
     if (warp == 0) {
-        for (int w = 1; w < TER_WARPS; ++w) {
-            const float ob = mb[w * 32 + lane];
-            const int ok = mk[w * 32 + lane];
-            if (ob < best || (ob == best && ok < bk)) {
-                best = ob;
-                bk = ok;
-            }
-        }
+        for (int w = 1; w < TER_WARPS; ++w) ter_take(mb[w * 32 + lane], mk[w * 32 + lane], best, bk);
     }
     return bk == 0x7fffffff ? -1 : bk;
 }
 
-// Shared memory of the territory kernels: the query tile and the warps' partial minima.
+// Shared memory of the territory kernels: the query tile, the candidate tile and the
+// warps' partial minima (the query and candidate tiles padded to ds coordinates).
 __host__ __device__ inline size_t territory_smem_bytes(int d)
 {
-    return sizeof(float) * (size_t)d * 33 + (sizeof(float) + sizeof(int)) * TER_WARPS * 32;
+    return sizeof(float) * (size_t)ter_ds(d) * (33 + TER_TILE) + (sizeof(float) + sizeof(int)) * TER_WARPS * 32;
 }
 
 // Walker w's new point (slot order[w]) stays only if its nearest surviving point
@@ -1021,28 +1075,44 @@ __global__ void __launch_bounds__(TER_WARPS * 32) k_territory(DevCtx C, int r0)
     __syncthreads();
     if (!s_mixed) return;
     const float *xs = C.fa + D.x_off;
+    const int ds = ter_ds(d);
     float *q = tsm;
-    float *mb = tsm + (size_t)d * 33;
+    float *ct = tsm + (size_t)ds * 33;
+    float *mb = ct + (size_t)ds * TER_TILE;
     int *mk = reinterpret_cast<int *>(mb + TER_WARPS * 32);
-    for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
-        const int j = e / d, c = e - j * d;
-        q[c * 33 + j] = (w0 + j < k) ? xs[(long)ord[w0 + j] * dp + c] : 0.f;
+    {
+        // warp w fills queries w, w + TER_WARPS, ...: the rows' addresses first, then the
+        // rows' loads in flight together, coalesced over the lanes
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const float *qp[TER_ROWS];
+#pragma unroll
+        for (int i = 0; i < TER_ROWS; ++i) {
+            const int j = warp + TER_WARPS * i;
+            qp[i] = (w0 + j < k) ? xs + (long)ord[w0 + j] * dp : nullptr;
+        }
+        for (int c = lane; c < ds; c += 32) {
+            float v[TER_ROWS];
+#pragma unroll
+            for (int i = 0; i < TER_ROWS; ++i) v[i] = (qp[i] != nullptr && c < d) ? qp[i][c] : 0.f;
+#pragma unroll
+            for (int i = 0; i < TER_ROWS; ++i) q[c * 33 + warp + TER_WARPS * i] = v[i];
+        }
     }
     __syncthreads();
     const int near = tile_nearest(q, d, n - k, [&](int i) { return xs + (long)ord[k + i] * dp; },
-                                  [&](int i) { return ord[k + i]; }, mb, mk);
+                                  [&](int i) { return ord[k + i]; }, mb, mk, ct);
     const int lane = threadIdx.x & 31, w = w0 + lane;
     const bool reject = (threadIdx.x < 32) && w < k && near >= 0 && lab[near] != C.new_label[D.w_off + w];
-    // the warps copy the rejected walkers' start points
+    // the warps copy the rejected walkers' start points (warp w: walkers w, w + TER_WARPS, ...)
     __shared__ int s_rej[32];
     if (threadIdx.x < 32) s_rej[lane] = reject ? 1 : 0;
     __syncthreads();
-    for (int j = 0; j < 32; ++j) {
+    for (int j = threadIdx.x >> 5; j < 32; j += TER_WARPS) {
         if (!s_rej[j]) continue;
         const int ww = w0 + j;
         const int slot = ord[ww], s0 = C.start_slot[D.w_off + ww];
-        for (int c = threadIdx.x; c < dp; c += blockDim.x) C.fa[D.x_off + (long)slot * dp + c] = xs[(long)s0 * dp + c];
-        if (threadIdx.x == 0) C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
+        for (int c = lane; c < dp; c += 32) C.fa[D.x_off + (long)slot * dp + c] = xs[(long)s0 * dp + c];
+        if (lane == 0) C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
     }
 }
 
@@ -1054,15 +1124,18 @@ __global__ void __launch_bounds__(TER_WARPS * 32) k_territory_plain(const float 
 {
     extern __shared__ float tsm[];
     const int w0 = blockIdx.x * 32;
+    const int ds = ter_ds(d);
     float *q = tsm;
-    float *mb = tsm + (size_t)d * 33;
+    float *ct = tsm + (size_t)ds * 33;
+    float *mb = ct + (size_t)ds * TER_TILE;
     int *mk = reinterpret_cast<int *>(mb + TER_WARPS * 32);
-    for (int e = threadIdx.x; e < 32 * d; e += blockDim.x) {
-        const int j = e / d, c = e - j * d;
-        q[c * 33 + j] = (w0 + j < k) ? xn[(long)(w0 + j) * d + c] : 0.f;
+    for (int e = threadIdx.x; e < 32 * ds; e += blockDim.x) {
+        const int j = e / ds, c = e - j * ds;
+        q[c * 33 + j] = (w0 + j < k && c < d) ? xn[(long)(w0 + j) * d + c] : 0.f;
     }
     __syncthreads();
-    const int near = tile_nearest(q, d, m_s, [&](int i) { return surv + (long)i * d; }, [&](int i) { return i; }, mb, mk);
+    const int near =
+        tile_nearest(q, d, m_s, [&](int i) { return surv + (long)i * d; }, [&](int i) { return i; }, mb, mk, ct);
     const int j = w0 + threadIdx.x;
     if (threadIdx.x < 32 && j < k) keep[j] = (near < 0 || surv_label[near] == want[j]) ? 1 : 0;
 }
@@ -1727,6 +1800,7 @@ __global__ void k_info(DevCtx C, int r, double logz, double *part)
     __shared__ double sh[32], sp[32];
     double h = 0.0, ps = 0.0;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (!gg_in(i, D.dead_cap, C.state + r)) break;
         const double ll = (double)D.dead_logl[D.dead_off + i];
         const double lp = D.dead_logw[D.dead_off + i] + ll - logz;
         const double p = exp(lp);
@@ -1831,6 +1905,7 @@ __global__ void k_export(DevCtx C, int r, int d, int d_pad, double logz, double 
     const long tot = n * d;
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
         const long i = e / d, c = e % d;
+        if (!gg_in(i, D.dead_cap, C.state + r)) break;
         if (x) x[e] = (double)D.dead_x[(D.dead_off + i) * d_pad + c];
         if (c == 0 && logp) logp[i] = D.dead_logw[D.dead_off + i] + (double)D.dead_logl[D.dead_off + i] - logz;
     }

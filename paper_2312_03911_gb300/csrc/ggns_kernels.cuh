@@ -665,9 +665,9 @@ __device__ __forceinline__ void mix_score8(const RunDesc &D, const ParView &P, f
 // lazy: for the mixture of up to 8 components g holds y and r_lane the responsibilities
 // on return, and mix_score8 forms the score when a reflection needs it; otherwise g is
 // the score.
-template <int KIND, int E>
+template <int KIND, int E, class Idle>
 __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&x)[E], float (&g)[E], int c0,
-                              const tc::State &T, tc::Pipe &pp, bool &ok, float &r_lane, bool &lazy)
+                              const tc::State &T, tc::Pipe &pp, bool &ok, float &r_lane, bool &lazy, const Idle &idle)
 {
     const bool mix = (KIND == NS_LIK_DENSE_MIX);
     // v is staged in g (the score is written only after the contraction)
@@ -685,13 +685,13 @@ __device__ float lik_dense_tc(const RunDesc &D, const ParView &P, const float (&
     lazy = false;
     if constexpr (KIND == NS_LIK_DENSE_MIX) {
         if (D.n_comp <= 8) {
-            ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, g);  // v is read before y is written
+            ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, g, idle);  // v is read before y is written
             lazy = true;
             return dense_mix_finish8<E>(D, P, x, g, r_lane);
         }
     }
     float y[E];
-    ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, y);
+    ok = tc::contract<E>(T, pp, g, D.d_pad, D.tc_sv, D.tc_inv, y, idle);
     return dense_finish<KIND, 32, E, true>(D, P, x, y, g, c0, nullptr);
 }
 
@@ -834,9 +834,12 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
                     // archive the dead point that this walker's output will replace
                     const int ks = C.order[D.pt_off + w];
                     const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
-                    float *ddst = D.dead_x + (D.dead_off + S->n_dead - W + w) * dp + c0;
+                    const long drow = S->n_dead - W + w;
+                    float *ddst = D.dead_x + (D.dead_off + drow) * dp + c0;
+                    const bool din = gg_in(drow, D.dead_cap, S);
 #pragma unroll
-                    for (int e = 0; e < E; ++e) ddst[e] = ksrc[e];
+                    for (int e = 0; e < E; ++e)
+                        if (din) ddst[e] = ksrc[e];
                 } else {
                     const float *ws = C.fa + D.ws_off + (long)w * 3 * dp + c0;
 #pragma unroll
@@ -1010,6 +1013,38 @@ __global__ void __launch_bounds__(HSS_THREADS) k_hss(DevCtx C, const int *run_li
 // time, so that no array of normals stays live (E a multiple of 4); `add` false
 // draws only the first block.  Returns the step's reservoir word (the spare bits of
 // the lane's first block).  The same update as with the normals drawn ahead.
+// The momentum noise of one step (all E normals of the lane and the reservoir word, the
+// same Philox blocks and Box-Muller pairs as noise_in_place).
+template <int E>
+__device__ __forceinline__ uint32_t draw_noise(const RunDesc &D, uint32_t iter, uint32_t slot, uint32_t step, int c0,
+                                               float (&z)[E])
+{
+    static_assert(E % 4 == 0, "whole Philox blocks");
+    uint32_t word = 0;
+#pragma unroll
+    for (int b = 0; b < E / 4; ++b) {
+        const U4 r = rng_block(D, iter, P_NOISE, slot, step, static_cast<uint32_t>((c0 >> 2) + b));
+        if (b == 0) word = spare_bits(r);
+        box_muller(r.x, r.y, z[4 * b], z[4 * b + 1]);
+        box_muller(r.z, r.w, z[4 * b + 2], z[4 * b + 3]);
+    }
+    return word;
+}
+
+// p takes the noise z of the step, as noise_in_place applies it.
+template <int E>
+__device__ __forceinline__ void apply_noise(const RunDesc &D, int c0, float keep, float dlt, const float (&z)[E],
+                                            float (&p)[E])
+{
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (D.noise_mode == 1)
+            p[e] = fmaf(keep, p[e], dlt * z[e] * ((c0 + e < D.d) ? 1.f : 0.f));
+        else
+            p[e] = p[e] * fmaf(dlt, z[e], 1.f);
+    }
+}
+
 template <int E>
 __device__ __forceinline__ uint32_t noise_in_place(const RunDesc &D, uint32_t iter, uint32_t slot, uint32_t step,
                                                    int c0, bool add, float keep, float dlt, float (&p)[E])
@@ -1127,6 +1162,9 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
     bool tc_ok = true;
     float tc_r = 0.f;      // responsibility of component lane % 8 (tensor-core mixture walk)
     bool tc_lazy = false;  // g holds y until the score is needed
+    __shared__ uint32_t s_nz_word[COOP_THREADS / 32];  // reservoir words of the stashed noise
+    __shared__ int s_nz_act[COOP_THREADS / 32];        // walkers stepping this loop round
+    int loop_i = 0;                                    // loop rounds so far (= t of the active walkers)
     if constexpr (TC) {
         // a CTA without walkers of this run leaves before it takes tensor memory
         if (static_cast<long>(blockIdx.x) * (blockDim.x / 32) >= W) return;
@@ -1202,9 +1240,12 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
                 // archive the dead point that this walker's output will replace
                 const int ks = C.order[D.pt_off + w];
                 const float *ksrc = C.fa + D.x_off + (long)ks * dp + c0;
-                float *ddst = D.dead_x + (D.dead_off + S->n_dead - W + w) * dp + c0;
+                const long drow = S->n_dead - W + w;
+                float *ddst = D.dead_x + (D.dead_off + drow) * dp + c0;
+                const bool din = gg_in(drow, D.dead_cap, S);
 #pragma unroll
-                for (int e = 0; e < E; ++e) ddst[e] = ksrc[e];
+                for (int e = 0; e < E; ++e)
+                    if (din) ddst[e] = ksrc[e];
                 // a rule already met before the first step registers at t = 0
                 reg_min = (D.min_ref == 0);
                 reg_max = (D.max_ref == 0 && D.min_steps <= 0);
@@ -1235,6 +1276,9 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             if (at_stop || t >= L) active = false;
         }
         if constexpr (COOP) {
+            if constexpr (TC) {
+                if (lane == 0) s_nz_act[grp] = active ? 1 : 0;
+            }
             if (!__syncthreads_or(active)) break;
             if constexpr (TC) {
                 if (s_tc_fail) {
@@ -1259,7 +1303,37 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         const bool lfold = fold_box<KIND, E, COOP>(D, P, x, p, c0);
         float ll;
         if constexpr (TC) {
-            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok, tc_r, tc_lazy);
+            // the warps without a pipeline role (warps STAGES + 1 ..) draw this step's
+            // momentum noise while P streams, their own and that of the warps with a role,
+            // and keep it in the walker's tensor-memory columns (the reservoir word in shared
+            // memory) until the step applies it.  Warp n's columns lie in the lanes of
+            // quarter n % 4, so the i-th role warp of a quarter is served by the (i mod h)-th
+            // idle warp of that quarter (h of them).  Active walkers of a CTA step in
+            // lock-step from t = 0: the step of every active walker is the loop count + 1.
+            auto idle = [&]() {
+                const int nw = static_cast<int>(blockDim.x >> 5);
+                const int q = grp & 3;
+                const int h0 = tc::STAGES + 1 + ((q - (tc::STAGES + 1)) % 4 + 4) % 4;  // first idle warp of quarter q
+                const int nh = (nw - 1 - h0) / 4 + 1;
+                const int mine = (grp - h0) / 4;
+                for (int i = -1, n = grp; n >= 0;) {
+                    if (s_nz_act[n]) {
+                        const uint32_t slot = static_cast<uint32_t>(blockIdx.x * nw + n);
+                        float z[E];
+                        const uint32_t wd = draw_noise<E>(D, iter, slot, static_cast<uint32_t>(loop_i + 1), c0, z);
+                        tc::tmem_store<E>(tc::noise_addr(T, n), z);
+                        if (lane == 0) s_nz_word[n] = wd;
+                    }
+                    // the next role warp of quarter q served by this warp
+                    for (n = -1, ++i; q + 4 * i <= tc::STAGES; ++i) {
+                        if (i % nh == mine) {
+                            n = q + 4 * i;
+                            break;
+                        }
+                    }
+                }
+            };
+            ll = lik_dense_tc<KIND, E>(D, P, x, g, c0, T, tc_pipe, tc_ok, tc_r, tc_lazy, idle);
         } else if constexpr (COOP) {
             ll = lik_dense_coop<KIND, E>(D, P, x, g, c0, rbuf, ptile, coop_tr);
         } else {
@@ -1339,7 +1413,18 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             // momentum noise (with noise_inside, an outside step only reflects)
             if constexpr (COOP) {
                 // one walker per warp: `stepping` is uniform over the warp
-                spare = noise_in_place<E>(D, iter, w, ts, c0, !(outside && D.noise_inside), keep, dlt, p);
+                if constexpr (TC) {
+                    // drawn during the contraction (published by its barriers)
+                    spare = s_nz_word[grp];
+                    if (!(outside && D.noise_inside)) {
+                        float z[E];
+                        tc::fence_after_sync();
+                        tc::tmem_load<E>(tc::noise_addr(T, grp), z);
+                        apply_noise<E>(D, c0, keep, dlt, z, p);
+                    }
+                } else {
+                    spare = noise_in_place<E>(D, iter, w, ts, c0, !(outside && D.noise_inside), keep, dlt, p);
+                }
                 res_word = __shfl_sync(0xffffffffu, spare, 0);
             } else if (!(outside && D.noise_inside)) {
                 if (D.noise_mode == 1) {
@@ -1362,9 +1447,10 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             }
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;
-            // record the step
-            if (!outside) row_store<E>(rec_x, x);
-            if (lig == 0) {
+            // record the step (row t of this walker's rec_len rows)
+            const bool rin = gg_in(t, R.rec_len, S);
+            if (!outside && rin) row_store<E>(rec_x, x);
+            if (lig == 0 && rin) {
                 // flags: bit 0 outside, bit 1 an inside step on which the box reflected the walker
                 *rec_meta = make_uint2(res_word, outside ? 1u : (folded ? 2u : 0u));
                 *rec_ll = ll;
@@ -1401,6 +1487,7 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             }
             t = ts;
         }
+        if constexpr (TC) ++loop_i;
     }
     if constexpr (TC) tc::teardown(T, tc_pipe);
 }
@@ -1517,7 +1604,7 @@ __global__ void __launch_bounds__(HSS_THREADS) k_grad_means(DevCtx C, int run, d
     const long n = S->n_dead;
     for (long base = (long)blockIdx.x * gpc; base < n; base += (long)gridDim.x * gpc) {
         const long i = base + grp;
-        const bool act = i < n;
+        const bool act = i < n && gg_in(i, D.dead_cap, C.state + run);
         const long ii = act ? i : 0;
         const double lp = act ? (D.dead_logw[D.dead_off + ii] + (double)D.dead_logl[D.dead_off + ii] - logz)
                               : -INFINITY;

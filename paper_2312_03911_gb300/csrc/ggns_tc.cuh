@@ -43,7 +43,7 @@ namespace tc {
 
 constexpr int WALKERS = 16;                    // N of every MMA: one walker per warp of a 512-thread CTA
 constexpr int STAGES = 4;                      // shared-memory stages of P (one producer warp each)
-constexpr uint32_t STAGE_BYTES = 32768;        // bytes of one stage
+constexpr uint32_t STAGE_BYTES = 32768;        // bytes of one stage (eight of 16 KB: 1.5x slower)
 constexpr uint64_t WAIT_NS = 2000000000ull;    // a wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -193,6 +193,59 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// A warp keeps E floats per lane (E = 4, 8 or 16) in its lanes of tensor memory at
+// column `col` (32x32b shape: lane l of the warp is tensor-memory lane 32 (warp % 4) + l),
+// or reads them back.
+template <int E>
+__device__ __forceinline__ void tmem_store(uint32_t taddr, const float (&v)[E])
+{
+    static_assert(E == 4 || E == 8 || E == 16, "4, 8 or 16 columns");
+    uint32_t r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) r[i] = __float_as_uint(v[i]);
+    if constexpr (E == 4) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                     "r"(r[2]), "r"(r[3])
+                     : "memory");
+    } else if constexpr (E == 8) {
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                     "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                     : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16};" ::"r"(taddr),
+            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+            "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+            : "memory");
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int E>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float (&v)[E])
+{
+    static_assert(E == 4 || E == 8 || E == 16, "4, 8 or 16 columns");
+    if constexpr (E == 16) {
+        tmem_load16(taddr, v);
+    } else {
+        uint32_t r[E];
+        if constexpr (E == 4) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                         : "r"(taddr));
+        } else {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = __uint_as_float(r[i]);
+    }
+}
+
 // The B operand of K-step j starts at byte vpos(j): 32 rows of 16 FP16 columns in four
 // groups of 8 rows (256 bytes apart), rows 0-15 the walkers' V1 and rows 16-31 their
 // V2 (V2 of walker n is row 16 + n, 512 bytes after its V1), 1 KB per K-step; one
@@ -235,7 +288,9 @@ struct State {
     uint64_t *full, *empty, *done;
     uint32_t *tmem_slot;
     uint32_t tmem;        // tensor-memory base address (lane 0, first column)
-    uint32_t ncols;       // allocated columns: accumulators P1V1, P1V2, P2V1 of 16 columns per M-tile
+    uint32_t ncols;       // allocated columns: accumulators P1V1, P1V2, P2V1 of 16 columns per M-tile,
+                          // then 64 columns where the walkers keep a step's momentum noise
+    uint32_t noise_col;   // first noise column (warp n: lanes 32 (n % 4) .., columns + 16 (n / 4))
     const float *ptc;     // pre-laid-out P of the run (global)
     int mt, ks, units, npos;
     int *fail;            // shared failure flag
@@ -246,6 +301,13 @@ struct State {
 __device__ __forceinline__ uint32_t acc_col(const State &T, int k, int m)
 {
     return static_cast<uint32_t>(k < 2 ? 2 * WALKERS * m + k * WALKERS : 2 * WALKERS * T.mt + WALKERS * m);
+}
+
+// The noise columns in tensor memory of the walker of warp n (lanes 32 (n % 4) .. + 31,
+// which warps n, n +- 4, n +- 8, ... can address).
+__device__ __forceinline__ uint32_t noise_addr(const State &T, int n)
+{
+    return T.tmem + (static_cast<uint32_t>(32 * (n & 3)) << 16) + T.noise_col + 16u * static_cast<uint32_t>(n >> 2);
 }
 
 // Each thread's view of the pipeline (32-bit counters, advanced incrementally): the
@@ -285,8 +347,9 @@ __device__ inline void setup(State &T, char *base, const float *ptc, int d_pad, 
         T.units = pl.units;
         T.npos = pl.npos;
         T.fail = fail_flag;
+        T.noise_col = static_cast<uint32_t>(3 * pl.mt * WALKERS);
         uint32_t nc = 32;
-        while (nc < static_cast<uint32_t>(3 * pl.mt * WALKERS)) nc <<= 1;  // a power of two
+        while (nc < T.noise_col + 4 * 16) nc <<= 1;  // a power of two
         T.ncols = nc;
         *fail_flag = 0;
         for (int s = 0; s < STAGES; ++s) {
@@ -374,7 +437,7 @@ __device__ inline void issue_mmas(const State &T, Pipe &pp)
             const uint32_t acc = j > 0 ? 1u : 0u;
             const uint64_t b = d0 + vb + vj;  // rows 0-15 (V1), or 0-31 (V1 and V2) with N = 32
             const uint64_t a0 = d0 + sa + static_cast<uint32_t>(u * MT) * 256u;
-            if ((u & 1) == 0) {  // UNITS is even: the parity of q is that of u
+            if ((q & 1) == 0) {
 #pragma unroll
                 for (int m = 0; m < MT; ++m) mma_f16(tmem + 2 * WALKERS * m, a0 + 256u * m, b, idesc32, acc);
             } else {
@@ -413,9 +476,11 @@ __device__ inline void refill_stage(const State &T, Pipe &pp, int w)
 // l E + E - 1 of walker n).  sv is the power of two s_v that scales v before the split
 // and tinv = 1 / (s_p s_v).  Every thread of the CTA calls it (barriers inside).
 // Returns false if a wait gave up (y is then undefined).
-template <int E>
+// `idle()` runs in the warps that neither issue MMAs nor refill stages, while the
+// contraction streams (work that the step needs later and that does not depend on y).
+template <int E, class Idle>
 __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], int d_pad, float sv, float tinv,
-                                float (&y)[E])
+                                float (&y)[E], const Idle &idle)
 {
     static_assert(E % 4 == 0, "quads of columns");
     static_assert(STAGES + 1 <= WALKERS, "a producer warp per stage besides the issuing warp");
@@ -452,6 +517,8 @@ __device__ inline bool contract(const State &T, Pipe &pp, const float (&v)[E], i
             }
         }
         __syncwarp();
+    } else {
+        idle();
     }
     pp.s0 = (pp.s0 + T.npos) % STAGES;
     // every thread: the accumulators are complete

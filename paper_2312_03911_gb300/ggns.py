@@ -21,9 +21,9 @@ import numpy as np
 from . import build as _build
 
 NS_OK, NS_ERR_ARG, NS_ERR_CUDA, NS_ERR_OOM, NS_ERR_TIMEOUT, NS_ERR_STUCK, NS_ERR_NUMERIC, NS_ERR_NOT_DONE, \
-    NS_ERR_CAPACITY = range(9)
+    NS_ERR_CAPACITY, NS_ERR_BOUNDS = range(10)
 STATUS_NAMES = ["NS_OK", "NS_ERR_ARG", "NS_ERR_CUDA", "NS_ERR_OOM", "NS_ERR_TIMEOUT", "NS_ERR_STUCK",
-                "NS_ERR_NUMERIC", "NS_ERR_NOT_DONE", "NS_ERR_CAPACITY"]
+                "NS_ERR_NUMERIC", "NS_ERR_NOT_DONE", "NS_ERR_CAPACITY", "NS_ERR_BOUNDS"]
 LIK_ISO_GAUSS, LIK_MIX_ISO, LIK_DENSE_GAUSS, LIK_DENSE_MIX, LIK_ROSENBROCK, LIK_TORUS = range(6)
 
 
