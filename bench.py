@@ -50,13 +50,13 @@ FP32_LANES_PER_SM = 128
 # traffic of a launch grows with the point-steps it takes; scaled to the timed launches' mean),
 # c2 per launch (one launch of the timed batch).
 TRAFFIC = {
-    "c5": {"bytes_per_point_step": 1663.59,
-           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "f41d3e69d9233436",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "6e93cfbb66cf0153",
+    "c5": {"bytes_per_point_step": 1656.15,
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "01dddb95bfcaded2",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "d463a32a030e2a3b",
                        "paper_2312_03911_gb300/csrc/ggns_tc.cuh": "c425a27c121efb13"}},
     "c2": {"bytes_per_launch": 83.198208e6,
-           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "f41d3e69d9233436",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "6e93cfbb66cf0153"}},
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "01dddb95bfcaded2",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "d463a32a030e2a3b"}},
 }
 
 
