@@ -56,7 +56,7 @@ class CfgT(C.Structure):
                 ("max_iters", C.c_int), ("noise_mode", C.c_int),
                 ("out_lo", C.c_double), ("out_hi", C.c_double), ("periodic", C.c_int), ("keep_last", C.c_int),
                 ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int),
-                ("box_fold", C.c_int), ("fold_counts", C.c_int)]
+                ("box_fold", C.c_int), ("fold_counts", C.c_int), ("midpoint", C.c_int)]
 
 
 class BatchStatsT(C.Structure):
@@ -106,6 +106,9 @@ def lib():
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int),
                                         C.POINTER(BatchStatsT), C.POINTER(C.c_double)]
             L.orc_reflect.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.orc_walk_step.argtypes = [C.POINTER(LikT), C.c_double, C.c_int, C.c_double, C.c_double,
+                                        C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.orc_walk_step.restype = C.c_int
             L.orc_sort_by_logl.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
             L.orc_knn_components.restype = C.c_int
             L.orc_knn_components.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int)]
@@ -181,7 +184,7 @@ def make_cfg(**kw) -> CfgT:
     c = dict(n_live=200, n_steps=1000, min_steps=0, dt_init=0.1, delta_p=0.05, tol=0.01, min_ref=1, max_ref=3,
              prune_after=10, termination=0, clustering=0, seed=0, run_id=0, max_iters=100000,
              noise_mode=0, out_lo=0.05, out_hi=0.15, periodic=0, keep_last=0, noise_inside=0, pick_all=0, territory=0, box_fold=0,
-             fold_counts=0)
+             fold_counts=0, midpoint=0)
     c.update(kw)
     return CfgT(**c)
 
@@ -221,6 +224,15 @@ def hss_batch(lik: Likelihood, lo, hi, cfg: CfgT, it, x0, logl0, lstar, dt, trac
     if trace:
         out["trace"] = tr[: st.t_stop]
     return out
+
+
+def walk_step(lik: Likelihood, mode: int, lstar: float, dt: float, x, p):
+    """One deterministic step of the walk without noise or box (orc_walk_step): mode 0 as
+    Algorithm 5 prints it, mode 1 the symmetric splitting.  Returns (x', p', reflected)."""
+    x = np.array(x, dtype=np.float64)
+    p = np.array(p, dtype=np.float64)
+    r = lib().orc_walk_step(C.byref(lik.struct), lik.logdet(), int(mode), float(lstar), float(dt), _dp(x), _dp(p))
+    return x, p, bool(r)
 
 
 def reflect(p, n):

@@ -39,7 +39,9 @@
  * dead-point sequence, L_i X_i, as the hyper-parameter table of Appendix C
  * defines it.  The printed forms (noise on every step, the pick among saved
  * inside states only, no region check, the box as an outside region) remain
- * switches of orc_cfg_t.
+ * switches of orc_cfg_t.  An option, not the default: the time-reversible form of the
+ * step (midpoint: half move, reflection with the normal at the half step, half move),
+ * against which the printed step (move, then reflection at the new point) is compared.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), written here from its published
@@ -316,6 +318,41 @@ void orc_reflect(int d, double *p, const double *n)
 }
 
 /* ------------------------------------------------------------------------- */
+/* One deterministic step of the walk (no noise, no prior box)                 */
+/* ------------------------------------------------------------------------- */
+/* mode 0 (Algorithm 5): x += p dt, then, if the new x is outside the slice
+ * (log L <= L*), p is reflected with the normal n = grad log L / |grad log L|
+ * taken at the new x.  mode 1 (the symmetric splitting): x += p dt / 2, the same
+ * reflection test and normal at that half-step point, then x += p dt / 2.  The
+ * second is time-reversible: applied to (x', -p') it returns (x, -p).  Returns 1 if
+ * the step reflected.  Used by the reversibility pins. */
+int orc_walk_step(const orc_lik_t *lk, double logdetP, int mode, double lstar, double dt, double *x, double *p)
+{
+    const int d = lk->d;
+    double *g = (double *)malloc(sizeof(double) * d);
+    const double h = mode ? 0.5 * dt : dt;
+    for (int i = 0; i < d; ++i) x[i] += p[i] * h;
+    const double logl = orc_loglik_impl(lk, logdetP, x, g);
+    int refl = 0;
+    if (!(logl > lstar)) {
+        double gg = 0.0;
+        for (int i = 0; i < d; ++i) gg += g[i] * g[i];
+        const double gn = sqrt(gg);
+        if (gn > 0.0 && isfinite(gn)) {
+            for (int i = 0; i < d; ++i) g[i] /= gn;
+            orc_reflect(d, p, g);
+        } else {
+            for (int i = 0; i < d; ++i) p[i] = -p[i];
+        }
+        refl = 1;
+    }
+    if (mode)
+        for (int i = 0; i < d; ++i) x[i] += p[i] * h;
+    free(g);
+    return refl;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Batched Hamiltonian slice sampling (Algorithm 5)                           */
 /* ------------------------------------------------------------------------- */
 
@@ -340,6 +377,11 @@ typedef struct {
                          the box is an outside step that reflects off the violated faces */
     int fold_counts;  /* with box_fold: an inside step on which the box reflected the walker counts
                          as a reflection for the step-size control (not for n_ref or the pick) */
+    int midpoint;     /* 1: the time-reversible form of the step (an option, not the default):
+                         half move, reflection with the normal at the half step if that point is
+                         outside, half move; the states (saved, picked) are the whole-step points,
+                         the refresh noise acts on every state, and the picked state is tested
+                         against L* at the end (outside: the walker returns its start point) */
 } orc_cfg_t;
 
 typedef struct {
@@ -375,11 +417,142 @@ typedef struct {
  * If trace != NULL it receives, per step t and walker j, x then p then logL and
  * the outside flag: trace[((t-1)*n + j)*(2d+2) + ...], for t <= n_steps.
  */
+/* The prior box as an exact reflection on a position (box_fold): the path unfolded on
+ * a line of period 2w folds back; an odd number of crossings flips p_i. */
+static int fold_into_box(int d, const double *lo, const double *hi, double *xj, double *pj)
+{
+    int folded = 0;
+    for (int i = 0; i < d; ++i) {
+        if (xj[i] >= lo[i] && xj[i] <= hi[i]) continue;
+        folded = 1;
+        const double w = hi[i] - lo[i];
+        double u = fmod(xj[i] - lo[i], 2.0 * w);
+        if (u < 0.0) u += 2.0 * w;
+        if (u > w) { xj[i] = lo[i] + (2.0 * w - u); pj[i] = -pj[i]; }
+        else xj[i] = lo[i] + u;
+    }
+    return folded;
+}
+
+/* Algorithm 5 with the time-reversible step (cfg->midpoint; see orc_walk_step mode 1):
+ * the walker's state m moves half a step to z, where log L and its gradient are
+ * evaluated (the reflection test, n_ref, the outside fraction), reflects there if z is
+ * outside, moves the second half step, and takes the refresh noise
+ * p <- sqrt(1 - dp^2) p + dp eps.  The prior box reflects exactly on both half moves.
+ * The saving window, the global stop and the size-1 reservoir are those of
+ * orc_hss_batch, over every step's state m; the drawn state is tested against L* at
+ * the end and, outside, the walker returns its start point (trace rows hold m, p, the
+ * log L at z and the outside flag of z). */
+static int hss_batch_mid(const orc_lik_t *lk, double logdetP, const double *lo, const double *hi,
+                         const orc_cfg_t *cfg, uint32_t iter, int n, const double *x0, const double *logl0,
+                         double lstar, double dt, double *x_out, double *logl_out, int *steps_out,
+                         orc_batch_stats_t *st, double *trace)
+{
+    const int d = lk->d;
+    const size_t nd = (size_t)n * d;
+    double *m = (double *)malloc(sizeof(double) * nd);
+    double *p = (double *)malloc(sizeof(double) * nd);
+    double *xr = (double *)malloc(sizeof(double) * nd);
+    double *z = (double *)malloc(sizeof(double) * d);
+    double *g = (double *)malloc(sizeof(double) * d);
+    double *eps = (double *)malloc(sizeof(double) * d);
+    int *n_ref = (int *)calloc(n, sizeof(int));
+    int *consec = (int *)calloc(n, sizeof(int));
+    int *count = (int *)calloc(n, sizeof(int));
+    long n_in = 0, n_out = 0, n_fold = 0;
+    int t_save = 0, t = 0, saving = 0;
+    memcpy(m, x0, sizeof(double) * nd);
+    for (int j = 0; j < n; ++j)
+        orc_normals(cfg->seed, cfg->run_id, iter, ORC_P_MOM, (uint32_t)j, 0, d, p + (size_t)j * d);
+    const double keep = sqrt(1.0 - cfg->delta_p * cfg->delta_p);
+    for (;;) {
+        int min_ref_now = n_ref[0];
+        for (int j = 1; j < n; ++j) if (n_ref[j] < min_ref_now) min_ref_now = n_ref[j];
+        if (n == 0 || t >= cfg->n_steps) break;
+        if (min_ref_now >= cfg->max_ref && t >= cfg->min_steps) break;
+        ++t;
+        for (int j = 0; j < n; ++j) {
+            double *mj = m + (size_t)j * d, *pj = p + (size_t)j * d;
+            for (int i = 0; i < d; ++i) z[i] = mj[i] + 0.5 * pj[i] * dt;
+            int folded = fold_into_box(d, lo, hi, z, pj);
+            const double logl = orc_loglik_impl(lk, logdetP, z, g);
+            const int out = !(logl > lstar);
+            if (out) {
+                double gg = 0.0;
+                for (int i = 0; i < d; ++i) gg += g[i] * g[i];
+                const double gn = sqrt(gg);
+                if (gn > 0.0 && isfinite(gn)) {
+                    for (int i = 0; i < d; ++i) g[i] /= gn;
+                    orc_reflect(d, pj, g);
+                } else {
+                    for (int i = 0; i < d; ++i) pj[i] = -pj[i];
+                }
+            }
+            for (int i = 0; i < d; ++i) mj[i] = z[i] + 0.5 * pj[i] * dt;
+            folded |= fold_into_box(d, lo, hi, mj, pj);
+            orc_normals(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, d, eps);
+            for (int i = 0; i < d; ++i) pj[i] = keep * pj[i] + cfg->delta_p * eps[i];
+            if (trace) {
+                double *tr = trace + ((size_t)(t - 1) * n + j) * (2 * d + 2);
+                for (int i = 0; i < d; ++i) { tr[i] = mj[i]; tr[d + i] = pj[i]; }
+                tr[2 * d] = logl; tr[2 * d + 1] = out;
+            }
+            n_ref[j] += out;
+            if (out) { ++n_out; ++consec[j]; } else { ++n_in; consec[j] = 0; n_fold += folded; }
+        }
+        if (!saving) {
+            int mr = n_ref[0];
+            for (int j = 1; j < n; ++j) if (n_ref[j] < mr) mr = n_ref[j];
+            if (mr >= cfg->min_ref) { saving = 1; t_save = t; }
+        }
+        for (int j = 0; j < n; ++j) {
+            if (saving) {
+                ++count[j];
+                uint32_t w[4];
+                orc_rng_block(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, 0, w);
+                uint32_t word = (w[0] & 511u) | ((w[1] & 511u) << 9) | ((w[2] & 511u) << 18) | ((w[3] & 31u) << 27);
+                if ((((uint64_t)word * (uint64_t)count[j]) >> 32) == 0)
+                    memcpy(xr + (size_t)j * d, m + (size_t)j * d, sizeof(double) * d);
+            }
+            if (cfg->prune_after > 0 && consec[j] >= cfg->prune_after) {
+                memcpy(m + (size_t)j * d, x0 + (size_t)j * d, sizeof(double) * d);
+                orc_normals(cfg->seed, cfg->run_id, iter, ORC_P_PRUNE, (uint32_t)j, (uint32_t)t, d,
+                            p + (size_t)j * d);
+                consec[j] = 0;
+            }
+        }
+    }
+    int n_fb = 0;
+    for (int j = 0; j < n; ++j) {
+        double l = -INFINITY;
+        if (count[j] > 0) l = orc_loglik_impl(lk, logdetP, xr + (size_t)j * d, g);
+        if (count[j] > 0 && l > lstar) {
+            memcpy(x_out + (size_t)j * d, xr + (size_t)j * d, sizeof(double) * d);
+            logl_out[j] = l;
+        } else {
+            memcpy(x_out + (size_t)j * d, x0 + (size_t)j * d, sizeof(double) * d);
+            logl_out[j] = logl0[j];
+            ++n_fb;
+        }
+        if (steps_out) steps_out[j] = t;
+    }
+    if (st) {
+        st->n_in = n_in; st->n_out = n_out; st->t_save = t_save; st->t_stop = t; st->n_fallback = n_fb;
+        st->n_fold = n_fold;
+    }
+    free(m); free(p); free(xr); free(z); free(g); free(eps);
+    free(n_ref); free(consec); free(count);
+    return 0;
+}
+
 int orc_hss_batch(const orc_lik_t *lk, double logdetP, const double *lo, const double *hi,
                   const orc_cfg_t *cfg, uint32_t iter, int n, const double *x0, const double *logl0,
                   double lstar, double dt, double *x_out, double *logl_out, int *steps_out,
                   orc_batch_stats_t *st, double *trace)
 {
+    if (cfg->midpoint && !cfg->periodic)
+        return hss_batch_mid(lk, logdetP, lo, hi, cfg, iter, n, x0, logl0, lstar, dt, x_out, logl_out, steps_out, st,
+                             trace);
     const int d = lk->d;
     const size_t nd = (size_t)n * d;
     double *x = (double *)malloc(sizeof(double) * nd);

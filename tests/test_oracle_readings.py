@@ -222,3 +222,44 @@ def test_box_reflection_counted_for_dt_keeps_high_dimensional_evidence_unbiased(
     truth = W.truth_logz_iso_mixture(np.zeros((1, d)), [0.1], None, -np.ones(d), np.ones(d))
     se = z.std(ddof=1) / math.sqrt(len(z))
     assert abs(z.mean() - truth) < 3.5 * se + 0.1, (z.mean() - truth, se)
+
+
+def test_symmetric_step_is_time_reversible_and_the_printed_step_is_not():
+    """The step of Algorithm 5 (move, then reflect with the normal at the new point) and its
+    symmetric splitting (half move, reflect at the half step, half move) near the contour of a
+    correlated Gaussian: from (x', -p') the symmetric step returns to (x, -p) whenever it
+    reflected; the printed step does not come back to x.  This is why the printed walk's evidence
+    offset grows with the trajectory length at d = 128 (oracle/trajectory_length.py)."""
+    d = 12
+    rng = np.random.default_rng(21)
+    prec, _, _, _ = W.dense_precision(rng, d, 1e-2, 1e-1)
+    lik = oracle.Likelihood(W.LIK_DENSE, d, means=np.zeros(d), precision=prec)
+    lstar = lik.loglik(np.zeros(d)) - 3.0
+    dt = 0.05
+    n_refl = {0: 0, 1: 0}
+    back_err = {0: [], 1: []}
+    for _ in range(400):
+        x = rng.standard_normal(d)
+        # a point close to the contour log L = L*, inside
+        lo_, hi_ = 0.0, 5.0
+        for _ in range(60):
+            mid = 0.5 * (lo_ + hi_)
+            (lo_, hi_) = (mid, hi_) if lik.loglik(mid * x) > lstar else (lo_, mid)
+        x = lo_ * x * 0.999
+        p = rng.standard_normal(d)
+        for mode in (0, 1):
+            x1, p1, r1 = oracle.walk_step(lik, mode, lstar, dt, x, p)
+            if not r1:
+                continue
+            n_refl[mode] += 1
+            x2, p2, _ = oracle.walk_step(lik, mode, lstar, dt, x1, -p1)
+            back_err[mode].append(max(np.abs(x2 - x).max(), np.abs(p2 + p).max()))
+    assert n_refl[0] > 50 and n_refl[1] > 50, n_refl
+    assert max(back_err[1]) < 1e-12, max(back_err[1])
+    assert np.median(back_err[0]) > 1e-3, np.median(back_err[0])
+
+
+def test_symmetric_walk_keeps_the_slice_uniform():
+    """The option midpoint (the time-reversible step, refresh noise on every state, the drawn
+    state tested against L* at the end) leaves a uniform ball slice uniform."""
+    assert abs(_ball_rank_z(dict(noise_mode=1, delta_p=0.5, pick_all=1, midpoint=1))) < 4
