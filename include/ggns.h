@@ -132,13 +132,23 @@ typedef struct {
                           the contraction on the tensor cores where d_pad is 128, 256 or 512,
                           else on CUDA cores; 1 on CUDA cores; -1 off (one read per walker)     */
     int runs_per_group;/* (context) runs per concurrent group and graph (0: all in one group)    */
+    /* The time-reversible form of Algorithm 5's step (an option; 0 keeps the step as printed):
+     * half move, reflection with the normal at the half step if that point is outside, half
+     * move; the refresh noise acts on every state; every step's state is recorded and the
+     * state the pick draws is tested against L* afterwards (outside: the start point).  The
+     * printed step (move, then reflect at the new point) is not time-reversible, and at high
+     * d its evidence offset grows with the trajectory length.  Needs box_fold 1, noise_mode 1,
+     * keep_last 0, a non-periodic kind and the single-pass walk with records for every step
+     * (NS_ERR_ARG otherwise). */
+    int midpoint;
 } ns_config;
 
 /* Fills the defaults: n_live 200, n_steps 1000, min_steps 0, dt_init 0.1,
  * delta_p 0.5, tol 0.01, min_ref 1, max_ref 3, prune_after 10, termination 0,
  * clustering 1, noise_mode 1, out_lo 0.05, out_hi 0.15, seed 0, run_id 0,
  * max_iters 100000, dead_cap 0, noise_inside 1, pick_all 1, territory 1,
- * keep_last 0, box_fold 0, fold_counts 0 and every launch choice 0 (the library's own). */
+ * keep_last 0, box_fold 0, fold_counts 0, every launch choice 0 (the library's own) and
+ * midpoint 0. */
 void ns_config_default(ns_config *cfg);
 
 /* Create a context for one run.  Copies the box, the likelihood parameters and

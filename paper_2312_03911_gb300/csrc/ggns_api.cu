@@ -125,6 +125,7 @@ struct ns_ctx {
     double hss_ms_sum = 0.0;
     bool any_clustering = false;
     bool any_territory = false;  // some run keeps new points in their cluster's region
+    bool any_midpoint = false;   // some run takes the time-reversible step (its picks are evaluated)
     int max_n = 0, max_d = 0;
     size_t sel_smem = 0, knn_smem = 0, cl_smem = 0, sort_smem = 0;
     cudaStream_t stream = nullptr;
@@ -245,6 +246,10 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
     }
     if (cfg.hss_mode < 0 || cfg.hss_mode > 2 || cfg.rec_len < 0 || cfg.noise_ahead < -1 || cfg.runs_per_group < 0)
         return fail(nullptr, NS_ERR_ARG, "launch choices out of range");
+    if (cfg.midpoint != 0 && (cfg.box_fold == 0 || cfg.noise_mode != 1 || cfg.keep_last != 0 ||
+                              lk.kind == NS_LIK_TORUS || cfg.hss_mode == 2))
+        return fail(nullptr, NS_ERR_ARG,
+                    "midpoint needs box_fold 1, noise_mode 1, keep_last 0, a non-periodic kind and the single pass");
     const int K = lk.n_comp;
     switch (lk.kind) {
     case NS_LIK_ISO_GAUSS:
@@ -500,6 +505,14 @@ ns_status launch_iteration(ns_ctx *ctx, Group &g, cudaStream_t s, int ev_slot, b
             CU(launch_hss_pick(C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, ctx->rec, ctx->rec_base_dev, s));
             ++n;
         }
+    // the reversible step: the drawn states are tested against L* (outside: the start point)
+    if (ctx->any_midpoint)
+        for (auto &cl : g.classes)
+            if (cl.single) {
+                CU(kind_launch(cl.kind).eval_new(cl.tile, C, cl.runs_dev, (int)cl.runs.size(), cl.max_k, cl.smem,
+                                                 cl.prec_in_smem, s));
+                ++n;
+            }
     for (int phase = 0; phase < 3; ++phase)
         for (auto &cl : g.classes) {
             if (cl.single && !cl.fallback) continue;  // records cover n_steps: no overflow
@@ -678,6 +691,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         D.keep_last = c.keep_last ? 1 : 0;
         D.box_fold = c.box_fold ? 1 : 0;
         D.fold_counts = c.fold_counts ? 1 : 0;
+        D.midpoint = c.midpoint ? 1 : 0;
         D.delta_p = (float)c.delta_p;
         D.keep = (float)std::sqrt(std::max(0.0, 1.0 - c.delta_p * c.delta_p));
         D.rosen_scale = (float)lik[r].rosen_scale;
@@ -714,6 +728,7 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         w += D.k;
         ctx->any_clustering |= (D.clustering != 0);
         ctx->any_territory |= (D.clustering != 0 && D.territory != 0);
+        ctx->any_midpoint |= (D.midpoint != 0);
         ctx->max_n = std::max(ctx->max_n, D.n_live);
         ctx->max_d = std::max(ctx->max_d, D.d);
     }
@@ -985,6 +1000,16 @@ ns_status ns_batch_create(int n_runs, const ns_prior_box *box, const ns_likeliho
         };
         CK(mkgroups());
     }
+    // the reversible step needs the single pass with records for every step (the three-phase
+    // kernels take the printed step)
+    for (auto &g : ctx->groups)
+        for (auto &cl : g.classes)
+            for (int r : cl.runs)
+                if (ctx->desc[r].midpoint && (!cl.single || cl.fallback)) {
+                    ns_destroy(ctx);
+                    return fail(nullptr, NS_ERR_ARG, "run %d: midpoint needs the single-pass walk with records for "
+                                                     "every step (resident walkers, rec_len >= n_steps)", r);
+                }
     ctx->sel_smem = select_smem_bytes(ctx->max_n);
     ctx->knn_smem = knn_smem_bytes(ctx->max_d);
     ctx->cl_smem = cluster_smem_bytes(ctx->max_n);
@@ -1662,6 +1687,8 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         const long gpc = HSS_THREADS / tile_of(D.tile).g;
         single = (n + gpc - 1) / gpc <= (long)per_sm * n_sm ? 1 : 0;
     }
+    if (D.midpoint && (!single || std::min(ctx->rec.rec_len, D.n_steps) < D.n_steps))
+        return fail(ctx, NS_ERR_ARG, "ns_hss: midpoint needs the single pass with records for every step");
     if (single) {
         R.rec_len = std::min(ctx->rec.rec_len, D.n_steps);
         R.xs = dp;
@@ -1677,6 +1704,8 @@ ns_status ns_hss(const ns_ctx *cctx, const float *x0_dev, const float *logl0_dev
         else
             CU(kind_launch(D.kind).hss1(D.tile, C, runs, 1, (int)n, R, rbase, rc.smem, rc.prec_in_smem, s));
         CU(launch_hss_pick(C, runs, 1, (int)n, R, rbase, s));
+        if (D.midpoint)
+            CU(kind_launch(D.kind).eval_new(D.tile, C, runs, 1, (int)n, rc.smem, rc.prec_in_smem, s));
     }
     for (int phase = 0; phase < 3; ++phase)
         CU(kind_launch(D.kind).hss(D.tile, C, runs, 1, (int)n, single ? (phase | 4) : phase, rc.smem,

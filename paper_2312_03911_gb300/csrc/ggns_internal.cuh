@@ -59,6 +59,8 @@ struct RunDesc {
     int noise_inside, pick_all, territory, keep_last;  // readings of Algorithm 5 (ns_config)
     int box_fold, fold_counts;                         // exact reflection off the prior box; its
                                                        // reflections in the step-size control
+    int midpoint;                                      // the time-reversible step (half move, reflection
+                                                       // at the half step, half move)
     float delta_p, keep, rosen_scale, lik_const;
     float torus_a, torus_b, torus_c;  // TORUS: sine and cosine frequencies, offset
     float tc_sv, tc_inv;              // tensor-core contraction: scale s_v of v, 1 / (s_p s_v)

@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         if (t <= tstop) m = R.meta[base + t - 1];
         const bool in_win = t <= tstop;
         const bool outside = in_win && (m.y & 1u) != 0u;
-        const bool saved = in_win && (!outside || D.pick_all) && t >= ts0;
+        const bool saved = in_win && (!outside || D.pick_all || D.midpoint) && t >= ts0;
         const unsigned smask = __ballot_sync(0xffffffffu, saved);
         const int cnt = count + __popc(smask & ((1u << lane) - 1u)) + 1;
         const bool acc = saved && (D.keep_last || ((static_cast<uint64_t>(m.x) * static_cast<uint64_t>(cnt)) >> 32) == 0);
@@ -930,7 +930,9 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
         nout += __popc(omask);
         nfold += __popc(fmask);
     }
-    if (pick_out) pick = 0;  // rejected: the walker keeps its start point
+    // rejected: the walker keeps its start point (with midpoint the drawn state is tested
+    // against L* by k_eval_new: the outside flag is that of the half step)
+    if (pick_out && !D.midpoint) pick = 0;
     const int slot = C.order[D.pt_off + w];
     if (!gg_in(slot, D.n_live, S) || !gg_in(C.start_slot[D.w_off + w], D.n_live, S)) return;
     float *dst = C.fa + D.x_off + (long)slot * dp;
@@ -939,6 +941,7 @@ __global__ void __launch_bounds__(PICK_WARPS * 32) k_hss_pick(DevCtx C, const in
     for (int c = lane; c < dp; c += 32) dst[c] = src[c];
     if (lane == 0) {
         C.logl[D.pt_off + slot] = (pick > 0) ? R.ll[base + pick - 1] : C.logl[D.pt_off + C.start_slot[D.w_off + w]];
+        if (D.midpoint) C.wint[(D.w_off + w) * WINT + 10] = (pick > 0) ? 1 : 0;
         C.label[D.pt_off + slot] = C.new_label[D.w_off + w];
         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_in), static_cast<unsigned long long>(tstop - nout));
         atomicAdd(reinterpret_cast<unsigned long long *>(&S->n_out), static_cast<unsigned long long>(nout));

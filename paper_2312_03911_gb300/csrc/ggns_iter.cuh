@@ -70,6 +70,9 @@ struct KindLaunch {
     cudaError_t (*hss1_coop)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, const RecView &R,
                              const long *rec_base, size_t smem, int tr, cudaStream_t s);
     cudaError_t (*hss1_coop_occ)(int tile, size_t smem, int tr, int *blocks_per_sm);
+    // the reversible step (midpoint): the pick's drawn states tested against L*
+    cudaError_t (*eval_new)(int tile, const DevCtx &C, const int *runs, int nr, int max_k, size_t smem, int pis,
+                            cudaStream_t s);
 };
 const KindLaunch &kind_launch(int kind);
 

@@ -8,7 +8,7 @@ const KindLaunch &kind_launch_densemix()
 {
     static const KindLaunch L{kind_densemix::prior, kind_densemix::hss, kind_densemix::lik, kind_densemix::grad, kind_densemix::smem_attr, kind_densemix::hss1,
                                 kind_densemix::hss1_occ, kind_densemix::hss1_coop,
-                                kind_densemix::hss1_coop_occ};
+                                kind_densemix::hss1_coop_occ, kind_densemix::eval_new};
     return L;
 }
 }  // namespace ggns

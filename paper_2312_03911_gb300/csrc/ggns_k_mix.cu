@@ -8,7 +8,7 @@ const KindLaunch &kind_launch_mix()
 {
     static const KindLaunch L{kind_mix::prior, kind_mix::hss, kind_mix::lik, kind_mix::grad, kind_mix::smem_attr, kind_mix::hss1,
                                 kind_mix::hss1_occ, kind_mix::hss1_coop,
-                                kind_mix::hss1_coop_occ};
+                                kind_mix::hss1_coop_occ, kind_mix::eval_new};
     return L;
 }
 }  // namespace ggns

@@ -753,6 +753,61 @@ __global__ void __launch_bounds__(HSS_THREADS) k_prior_init(DevCtx C, const int 
 }
 
 // ------------------------------------------------------------------------
+// The reversible step (midpoint): the state the pick drew for walker w (now in its
+// killed slot, flagged in wint[10]) is tested against L*; outside, the slot takes
+// the walker's start point and its log L back (the slice-sampling rejection).
+// One walker-tile group per walker.
+// ------------------------------------------------------------------------
+template <int KIND, int G, int E>
+__global__ void __launch_bounds__(HSS_THREADS) k_eval_new(DevCtx C, const int *run_list, int prec_in_smem)
+{
+    extern __shared__ float smem[];
+    const int r = run_list[blockIdx.y];
+    const RunDesc D = C.desc[r];
+    RunState *S = C.state + r;
+    if (S->done || !D.midpoint) return;
+    const ParView P = load_params(C, D, smem, prec_in_smem);
+    float *rbase = smem + param_smem_floats(D, prec_in_smem);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int lig = lane % G;
+    const int grp = threadIdx.x / G;
+    const int c0 = lig * E;
+    const int gpc = HSS_THREADS / G;
+    const int dp = D.d_pad;
+    float *rbuf = rbase + (long)grp * dp;
+    const float lstar = static_cast<float>(S->lstar);
+    for (int base = blockIdx.x * gpc; base < D.k; base += gridDim.x * gpc) {
+        const int w = base + grp;
+        const bool act = w < D.k;
+        const int ww = act ? w : 0;
+        int *flag = C.wint + (long)(D.w_off + ww) * WINT + 10;
+        const bool need = act && *flag != 0;
+        if (!__any_sync(0xffffffffu, need)) continue;  // the likelihood's group sums are warp-wide
+        const int slot = C.order[D.pt_off + ww];
+        float *xs = C.fa + D.x_off + (long)slot * dp + c0;
+        float x[E], g[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) x[e] = xs[e];
+        const float ll = lik_eval<KIND, G, E>(D, P, x, g, c0, rbuf, nullptr);
+        if (!need) continue;
+        if (ll > lstar) {
+            if (lig == 0) C.logl[D.pt_off + slot] = ll;
+        } else {
+            const int s0 = C.start_slot[D.w_off + ww];
+            const float *src = C.fa + D.x_off + (long)s0 * dp + c0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) xs[e] = src[e];
+            if (lig == 0) {
+                C.logl[D.pt_off + slot] = C.logl[D.pt_off + s0];
+                C.wint[(long)(D.w_off + ww) * WINT + 6] = 1;
+            }
+        }
+        if (lig == 0) *flag = 0;
+    }
+}
+
+// ------------------------------------------------------------------------
 // Batched Hamiltonian slice sampling (Algorithm 5), one of three phases:
 //   phase 0: from the start point until the walker's own n_ref >= min_ref;
 //            t_save = max over walkers of that step (the first step at which
@@ -1293,12 +1348,14 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
         // the registration count for the next stop test, read while this step runs
         if (stepping && reg_max && rem_seen != 0) rem_seen = *v_remain;
 
-        // ---- one step of Algorithm 5 (as in k_hss)
+        // ---- one step of Algorithm 5 (as in k_hss); with midpoint the time-reversible
+        // form: half move, the evaluation and the reflection at the half step, half move
         const int ts = t + 1;
         uint32_t res_word = 0;
         if constexpr (!COOP) res_word = __shfl_sync(0xffffffffu, spare, gbase);
+        const float hdt = D.midpoint ? 0.5f * dt : dt;
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], dt, x[e]);
+        for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], hdt, x[e]);
         wrap_periodic<KIND, E>(D, P, x, c0);
         const bool lfold = fold_box<KIND, E, COOP>(D, P, x, p, c0);
         float ll;
@@ -1409,24 +1466,36 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
                 for (int e = 0; e < E; ++e) p[e] = -p[e];
             }
         }
+        bool folded_all = folded;
+        if (D.midpoint) {
+            // the second half move to the step's state (the box reflects it exactly too)
+#pragma unroll
+            for (int e = 0; e < E; ++e) x[e] = fmaf(p[e], hdt, x[e]);
+            const bool lfold2 = fold_box<KIND, E, COOP>(D, P, x, p, c0);
+            // every lane takes the group sum (the groups of a warp differ in `folded`)
+            const int nf2 = gsum_i<G>(lfold2 ? 1 : 0);
+            folded_all = folded || nf2 != 0;
+        }
         if (stepping) {
-            // momentum noise (with noise_inside, an outside step only reflects)
+            // momentum noise (with noise_inside, an outside step only reflects; with midpoint
+            // every state takes the refresh)
+            const bool add_noise = D.midpoint || !(outside && D.noise_inside);
             if constexpr (COOP) {
                 // one walker per warp: `stepping` is uniform over the warp
                 if constexpr (TC) {
                     // drawn during the contraction (published by its barriers)
                     spare = s_nz_word[grp];
-                    if (!(outside && D.noise_inside)) {
+                    if (add_noise) {
                         float z[E];
                         tc::fence_after_sync();
                         tc::tmem_load<E>(tc::noise_addr(T, grp), z);
                         apply_noise<E>(D, c0, keep, dlt, z, p);
                     }
                 } else {
-                    spare = noise_in_place<E>(D, iter, w, ts, c0, !(outside && D.noise_inside), keep, dlt, p);
+                    spare = noise_in_place<E>(D, iter, w, ts, c0, add_noise, keep, dlt, p);
                 }
                 res_word = __shfl_sync(0xffffffffu, spare, 0);
-            } else if (!(outside && D.noise_inside)) {
+            } else if (add_noise) {
                 if (D.noise_mode == 1) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) p[e] = fmaf(keep, p[e], dlt * eps[e] * ((c0 + e < D.d) ? 1.f : 0.f));
@@ -1447,12 +1516,13 @@ __global__ void __launch_bounds__(COOP ? COOP_THREADS : HSS_THREADS, COOP ? 1 : 
             }
             nref += outside ? 1 : 0;
             consec = outside ? consec + 1 : 0;
-            // record the step (row t of this walker's rec_len rows)
+            // record the step (row t of this walker's rec_len rows): x of the inside steps, of
+            // every step with midpoint (its state, which the pick may draw)
             const bool rin = gg_in(t, R.rec_len, S);
-            if (!outside && rin) row_store<E>(rec_x, x);
+            if ((!outside || D.midpoint) && rin) row_store<E>(rec_x, x);
             if (lig == 0 && rin) {
                 // flags: bit 0 outside, bit 1 an inside step on which the box reflected the walker
-                *rec_meta = make_uint2(res_word, outside ? 1u : (folded ? 2u : 0u));
+                *rec_meta = make_uint2(res_word, outside ? 1u : (folded_all ? 2u : 0u));
                 *rec_ll = ll;
             }
             rec_x += R.xs;

@@ -56,6 +56,14 @@ static cudaError_t hss1_t(const DevCtx &C, const int *runs, int nr, int max_k, c
     return cudaGetLastError();
 }
 template <int G, int E>
+static cudaError_t eval_new_t(const DevCtx &C, const int *runs, int nr, int max_k, size_t smem, int pis, cudaStream_t s)
+{
+    const int gpc = HSS_THREADS / G;
+    const int bx = (max_k + gpc - 1) / gpc;
+    k_eval_new<KIND, G, E><<<dim3(bx, nr), HSS_THREADS, smem, s>>>(C, runs, pis);
+    return cudaGetLastError();
+}
+template <int G, int E>
 static cudaError_t occ_t(size_t smem, int *blocks_per_sm)
 {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hss1<KIND, G, E>, HSS_THREADS, smem);
@@ -70,6 +78,7 @@ static cudaError_t smem_t(size_t smem)
     if ((e = cudaFuncSetAttribute((const void *)k_hss<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute((const void *)k_hss1<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute((const void *)k_lik_points<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute((const void *)k_eval_new<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v)) != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void *)k_grad_means<KIND, G, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
 }
 
@@ -125,6 +134,11 @@ static cudaError_t hss1(int tile, const DevCtx &C, const int *runs, int nr, int 
 static cudaError_t hss1_occ(int tile, size_t smem, int *blocks_per_sm)
 {
     GGNS_DISPATCH(occ_t, smem, blocks_per_sm)
+}
+static cudaError_t eval_new(int tile, const DevCtx &C, const int *runs, int nr, int max_k, size_t smem, int pis,
+                            cudaStream_t s)
+{
+    GGNS_DISPATCH(eval_new_t, C, runs, nr, max_k, smem, pis, s)
 }
 
 // The CTA-cooperative single pass (dense kinds, one walker per warp): tiles 6, 7, 8.

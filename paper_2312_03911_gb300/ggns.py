@@ -47,7 +47,7 @@ class Config(C.Structure):
                 ("noise_inside", C.c_int), ("pick_all", C.c_int), ("territory", C.c_int), ("keep_last", C.c_int),
                 ("box_fold", C.c_int), ("fold_counts", C.c_int),
                 ("tile", C.c_int), ("hss_mode", C.c_int), ("rec_len", C.c_int), ("noise_ahead", C.c_int),
-                ("coop", C.c_int), ("runs_per_group", C.c_int)]
+                ("coop", C.c_int), ("runs_per_group", C.c_int), ("midpoint", C.c_int)]
 
 
 class Result(C.Structure):

@@ -64,6 +64,7 @@ VARIANTS = [
     ("printed noise and pick", dict(noise_mode=0, delta_p=0.05, noise_inside=0, pick_all=0, territory=0)),
     ("exact box reflection", dict(box_fold=1)),
     ("exact box reflection, folds counted for dt", dict(box_fold=1, fold_counts=1)),
+    ("time-reversible step", dict(box_fold=1, midpoint=1)),
 ]
 
 

@@ -632,6 +632,60 @@ def test_tensor_core_dense_trajectories_match_oracle(kind, d, n, steps):
     np.testing.assert_allclose(lo_.cpu().numpy(), o["logl"], rtol=1e-5, atol=1e-3)
 
 
+@pytest.mark.parametrize("kind,d,n,steps,dt", [("iso", 8, 40, 20, 0.02), ("mix", 33, 40, 20, 0.02),
+                                               ("dense", 128, 32, 20, 0.004), ("dense_mix", 512, 24, 10, 0.004)])
+def test_reversible_step_trajectories_match_oracle(kind, d, n, steps, dt):
+    """The time-reversible form of the step (midpoint: half move, reflection at the half step,
+    half move; refresh on every state; the drawn state tested against L* after the pick) on the
+    per-walker walk and on the tensor-core walk: at most 20 steps from identical FP32 inputs give
+    the oracle's step window, in/out/fold counts and outputs within 1e-5."""
+    w = W.small_workload(kind, d, 2 * n, seed=19)
+    w = dict(w, cfg=dict(w["cfg"], n_steps=steps, midpoint=1, box_fold=1))
+    lik = oracle.Likelihood.from_spec(w["spec"])
+    rng = np.random.default_rng(8)
+    center = np.asarray(w["spec"]["means"])[0]
+    found = False
+    for attempt in range(40):
+        x0 = np.clip(center + _ball_start(d, n, 0.05, rng), -0.99, 0.99).astype(np.float32).astype(np.float64)
+        l0 = np.array([lik.loglik(v) for v in x0])
+        lstar = float(np.float32(np.min(l0) - 1.0))
+        o = oracle.hss_batch(lik, w["lo"], w["hi"], oracle.make_cfg(**w["cfg"]), 3, x0, l0, lstar, dt, trace=True)
+        # decisions away from L* on both sides: the half-step values along the trajectories and
+        # the values of the states the walkers return
+        ll = o["trace"][:, :, 2 * d]
+        margin = 1e-5 * max(1.0, abs(lstar)) + 1e-3
+        # ... and a saving window that opens (every walker reflects min_ref times)
+        if (o["t_save"] > 0 and np.min(np.abs(ll - lstar)) > margin and
+                np.min(np.abs(o["logl"] - lstar)) > margin):
+            found = True
+            break
+    assert found
+    s = ggns.Sampler([w])
+    if d >= 128:
+        assert s.profile()["tensor_classes"] == 1
+    xo = torch.zeros((n, d), device="cuda")
+    lo_ = torch.zeros(n, device="cuda")
+    x0d, l0d = _dev(x0, torch.float32), _dev(l0, torch.float32)
+    st = s.hss(x0d.data_ptr(), l0d.data_ptr(), n, lstar, dt, 3, xo.data_ptr(), lo_.data_ptr())
+    assert o["n_out"] > 20  # the reflection at the half step is exercised
+    assert (st["t_save"], st["t_stop"]) == (o["t_save"], o["t_stop"])
+    assert (st["n_in"], st["n_out"], st["n_fold"]) == (o["n_in"], o["n_out"], o["n_fold"])
+    np.testing.assert_allclose(xo.cpu().numpy(), o["x"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(lo_.cpu().numpy(), o["logl"], rtol=1e-5, atol=1e-3)
+
+
+def test_reversible_step_option_checks():
+    """midpoint with the printed noise, with keep_last, or on the torus is refused at creation."""
+    for over in (dict(midpoint=1, box_fold=1, noise_mode=0), dict(midpoint=1, box_fold=0),
+                 dict(midpoint=1, box_fold=1, keep_last=1)):
+        w = W.small_workload("iso", 4, 50, seed=2)
+        with pytest.raises(ggns.GGNSError):
+            ggns.Sampler([dict(w, cfg=dict(w["cfg"], **over))])
+    wt = W.small_workload("torus", 4, 50, seed=2)
+    with pytest.raises(ggns.GGNSError):
+        ggns.Sampler([dict(wt, cfg=dict(wt["cfg"], midpoint=1, box_fold=1))])
+
+
 # ---------------------------------------------------------------- dense configurations at full size
 def _sampled_logl_check(s, w, n=64, seed=3):
     """Sampled dead points: the fused FP32 likelihood (the walkers' per-walker evaluation, which
