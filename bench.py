@@ -51,12 +51,12 @@ FP32_LANES_PER_SM = 128
 # c2 per launch (one launch of the timed batch).
 TRAFFIC = {
     "c5": {"bytes_per_point_step": 1656.15,
-           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "01dddb95bfcaded2",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "d463a32a030e2a3b",
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "377883e806dbcbd2",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "2cb53c1f2bf11a28",
                        "paper_2312_03911_gb300/csrc/ggns_tc.cuh": "c425a27c121efb13"}},
     "c2": {"bytes_per_launch": 83.198208e6,
-           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "01dddb95bfcaded2",
-                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "d463a32a030e2a3b"}},
+           "sources": {"paper_2312_03911_gb300/csrc/ggns_kernels.cuh": "377883e806dbcbd2",
+                       "paper_2312_03911_gb300/csrc/ggns_internal.cuh": "2cb53c1f2bf11a28"}},
 }
 
 
