@@ -2,12 +2,12 @@
 
 Correlated Gaussians of the c3 family (Sigma = Q diag(lambda) Q^T, lambda log-uniform in
 [1e-3, 1e-1], mean U[-0.3, 0.3]) in d dimensions on [-1, 1]^d, n_live 500, the prior box
-as an exact reflection, 8 seeded runs with max_ref 3 and with max_ref 9: the mean log Z
+as an exact reflection, 8 (--seeds) seeded runs with max_ref 3 and with max_ref 9: the mean log Z
 minus the closed form, its standard error, the spread, the stated error and the
 likelihood evaluations.  With --midpoint the walk takes the time-reversible step (the
 oracle's midpoint option) instead of the printed one.
 
-    python oracle/trajectory_length.py 128 [--midpoint]
+    python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8]
 """
 import math, multiprocessing as mp, os, sys, time
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -31,7 +31,8 @@ if __name__ == "__main__":
     import oracle; oracle.build()
     d = int(sys.argv[1]) if len(sys.argv) > 1 else 32
     mid = int("--midpoint" in sys.argv)
-    jobs = [(d, 500, mr, r, fold, mid) for mr in (3, 9) for fold in (1,) for r in range(8)]
+    seeds = int(sys.argv[sys.argv.index("--seeds") + 1]) if "--seeds" in sys.argv else 8
+    jobs = [(d, 500, mr, r, fold, mid) for mr in (3, 9) for fold in (1,) for r in range(seeds)]
     t0 = time.time()
     with mp.get_context("spawn").Pool(os.cpu_count()) as pool:
         res = pool.map(one, jobs, chunksize=1)
