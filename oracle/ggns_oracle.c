@@ -442,7 +442,10 @@ static int fold_into_box(int d, const double *lo, const double *hi, double *xj, 
  * The saving window, the global stop and the size-1 reservoir are those of
  * orc_hss_batch, over every step's state m; the drawn state is tested against L* at
  * the end and, outside, the walker returns its start point (trace rows hold m, p, the
- * log L at z and the outside flag of z). */
+ * log L at z and the outside flag of z).  keep_last (the App. G fixed-step ablation)
+ * keeps the last state of the window in place of the reservoir's draw; with a fixed
+ * number of steps (max_ref out of reach, min_ref 0, no pruning) the walk is then a
+ * fixed-length reversible trajectory whose end point is accepted when inside. */
 static int hss_batch_mid(const orc_lik_t *lk, double logdetP, const double *lo, const double *hi,
                          const orc_cfg_t *cfg, uint32_t iter, int n, const double *x0, const double *logl0,
                          double lstar, double dt, double *x_out, double *logl_out, int *steps_out,
@@ -511,7 +514,7 @@ static int hss_batch_mid(const orc_lik_t *lk, double logdetP, const double *lo, 
                 uint32_t w[4];
                 orc_rng_block(cfg->seed, cfg->run_id, iter, ORC_P_NOISE, (uint32_t)j, (uint32_t)t, 0, w);
                 uint32_t word = (w[0] & 511u) | ((w[1] & 511u) << 9) | ((w[2] & 511u) << 18) | ((w[3] & 31u) << 27);
-                if ((((uint64_t)word * (uint64_t)count[j]) >> 32) == 0)
+                if (cfg->keep_last || (((uint64_t)word * (uint64_t)count[j]) >> 32) == 0)
                     memcpy(xr + (size_t)j * d, m + (size_t)j * d, sizeof(double) * d);
             }
             if (cfg->prune_after > 0 && consec[j] >= cfg->prune_after) {

@@ -5,38 +5,62 @@ Correlated Gaussians of the c3 family (Sigma = Q diag(lambda) Q^T, lambda log-un
 as an exact reflection, 8 (--seeds) seeded runs with max_ref 3 and with max_ref 9: the mean log Z
 minus the closed form, its standard error, the spread, the stated error and the
 likelihood evaluations.  With --midpoint the walk takes the time-reversible step (the
-oracle's midpoint option) instead of the printed one.
+oracle's midpoint option) instead of the printed one; --first N starts the run ids at N (new
+replicas beside earlier ones), --max-ref M runs that one trajectory length only, and --fixed K
+runs trajectories of exactly K steps that keep their last state (keep_last, min_ref 0, max_ref
+out of reach, no pruning) in place of the window.  Beside the offset each line gives the
+fraction of walkers that returned their start point and the mean steps per walker.
 
-    python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8]
+    python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8] [--first 0] [--max-ref 9 | --fixed 60]
 """
 import math, multiprocessing as mp, os, sys, time
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import numpy as np
 
 def one(args):
-    d, n_live, max_ref, rid, fold, mid = args
+    d, n_live, mode, val, rid, mid = args
     import oracle
     from paper_2312_03911_gb300 import workloads as W
     rng = np.random.default_rng(W.SEED_BASE + 3)
     prec, _, _, _ = W.dense_precision(rng, d)
     spec = dict(kind=W.LIK_DENSE, d=d, means=rng.uniform(-0.3, 0.3, size=(1, d)), precision=prec)
     lik = oracle.Likelihood.from_spec(spec)
-    over = dict(W.BOX_FOLD) if fold else {}
-    cfg = oracle.make_cfg(**dict(W.DEFAULT_CFG, n_live=n_live, clustering=0, seed=4242, run_id=rid, max_ref=max_ref, midpoint=mid, **over))
+    if mode == "max_ref":
+        walk = dict(max_ref=val)
+    else:
+        walk = dict(keep_last=1, min_ref=0, max_ref=10**9, n_steps=val, min_steps=val, prune_after=0)
+    cfg = oracle.make_cfg(**dict(W.DEFAULT_CFG, n_live=n_live, clustering=0, seed=4242, run_id=rid, midpoint=mid,
+                                 **dict(W.BOX_FOLD, **walk)))
     r = oracle.run(lik, -np.ones(d), np.ones(d), cfg)
     truth = W.truth_logz(dict(name="x", spec=spec, lo=-np.ones(d), hi=np.ones(d), cfg={}))
-    return d, max_ref, fold, r["logz"] - truth, r["logz_err"], r["n_like"], r["status"]
+    walkers = max(r["n_dead"] - n_live, 1)
+    return ((mode, val), r["logz"] - truth, r["logz_err"], r["n_like"], r["status"],
+            r["n_fallback"] / walkers, r["n_steps_total"] / walkers)
+
+def _arg(name, default):
+    return int(sys.argv[sys.argv.index(name) + 1]) if name in sys.argv else default
 
 if __name__ == "__main__":
     import oracle; oracle.build()
     d = int(sys.argv[1]) if len(sys.argv) > 1 else 32
     mid = int("--midpoint" in sys.argv)
-    seeds = int(sys.argv[sys.argv.index("--seeds") + 1]) if "--seeds" in sys.argv else 8
-    jobs = [(d, 500, mr, r, fold, mid) for mr in (3, 9) for fold in (1,) for r in range(seeds)]
+    seeds, first = _arg("--seeds", 8), _arg("--first", 0)
+    if "--fixed" in sys.argv:
+        groups = [("fixed", _arg("--fixed", 0))]
+    elif "--max-ref" in sys.argv:
+        groups = [("max_ref", _arg("--max-ref", 0))]
+    else:
+        groups = [("max_ref", 3), ("max_ref", 9)]
+    jobs = [(d, 500, m, v, r, mid) for m, v in groups for r in range(first, first + seeds)]
     t0 = time.time()
     with mp.get_context("spawn").Pool(os.cpu_count()) as pool:
         res = pool.map(one, jobs, chunksize=1)
-    for mr in (3, 9):
-        z = np.array([x[3] for x in res if x[1] == mr]); e = np.mean([x[4] for x in res if x[1] == mr]); nl = np.mean([x[5] for x in res if x[1] == mr])
-        print(f"d {d} max_ref {mr}: offset {z.mean():+.3f} +- {z.std(ddof=1)/math.sqrt(len(z)):.3f} sd {z.std(ddof=1):.3f} stated {e:.3f} n_like {nl:.3g} status {[x[6] for x in res if x[1]==mr]}", flush=True)
+    for g in groups:
+        rows = [x for x in res if x[0] == g]
+        z = np.array([x[1] for x in rows])
+        print(f"d {d} {g[0]} {g[1]}: offset {z.mean():+.3f} +- {z.std(ddof=1)/math.sqrt(len(z)):.3f} "
+              f"sd {z.std(ddof=1):.3f} stated {np.mean([x[2] for x in rows]):.3f} "
+              f"n_like {np.mean([x[3] for x in rows]):.3g} start-point returns {np.mean([x[5] for x in rows]):.3f} "
+              f"steps/walker {np.mean([x[6] for x in rows]):.1f} status {[x[4] for x in rows]}", flush=True)
+        print("  per run:", " ".join(f"{v:+.3f}" for v in z), flush=True)
     print("took", time.time() - t0)

@@ -263,3 +263,24 @@ def test_symmetric_walk_keeps_the_slice_uniform():
     """The option midpoint (the time-reversible step, refresh noise on every state, the drawn
     state tested against L* at the end) leaves a uniform ball slice uniform."""
     assert abs(_ball_rank_z(dict(noise_mode=1, delta_p=0.5, pick_all=1, midpoint=1))) < 4
+
+
+def test_fixed_length_symmetric_walk_keeps_the_slice_uniform():
+    """The reversible step with keep_last over a fixed number of steps (min_ref 0, max_ref out
+    of reach, no pruning): the end point of a fixed-length reversible trajectory, accepted when
+    inside and otherwise replaced by the start point, leaves a uniform ball slice uniform, and
+    the walker's output is its state after exactly that many steps."""
+    fixed = dict(noise_mode=1, delta_p=0.5, pick_all=1, midpoint=1, keep_last=1, min_ref=0,
+                 max_ref=10**6, n_steps=30, min_steps=30, prune_after=0)
+    assert abs(_ball_rank_z(fixed)) < 4
+    lik, lstar = _ball(6)
+    rng = np.random.default_rng(9)
+    x0 = _uniform_ball(rng, 32, 6, 0.3)
+    cfg = oracle.make_cfg(**dict(fixed, seed=3, n_steps=12, min_steps=12))
+    o = oracle.hss_batch(lik, -np.ones(6), np.ones(6), cfg, 0, x0, [lik.loglik(q) for q in x0], lstar, 0.03,
+                         trace=True)
+    last = o["trace"][11, :, :6]
+    inside = np.array([lik.loglik(q) > lstar for q in last])
+    assert o["t_stop"] == 12 and 0 < inside.sum() < 32
+    np.testing.assert_array_equal(o["x"][inside], last[inside])
+    np.testing.assert_array_equal(o["x"][~inside], x0[~inside])
