@@ -114,7 +114,8 @@ typedef struct {
                           0: drawn uniformly over the saved inside states only (Algorithm 5)     */
     int territory;     /* 1: with several clusters alive, a new point whose nearest surviving
                           point belongs to another cluster returns its start point               */
-    int keep_last;     /* Appendix G ablation: 1 returns the last inside state of the window     */
+    int keep_last;     /* Appendix G ablation: 1 returns the last inside state of the window
+                          (with midpoint: the last state, tested against L* like any pick)      */
     int box_fold;      /* 0: leaving the prior box is an outside step, reflected off the violated faces
                           1: the box reflects a walker exactly (its position folds back across the
                           face, that momentum component flips; no outside step), so only the
@@ -138,8 +139,13 @@ typedef struct {
      * state the pick draws is tested against L* afterwards (outside: the start point).  The
      * printed step (move, then reflect at the new point) is not time-reversible, and at high
      * d its evidence offset grows with the trajectory length.  Needs box_fold 1, noise_mode 1,
-     * keep_last 0, a non-periodic kind and the single-pass walk with records for every step
-     * (NS_ERR_ARG otherwise). */
+     * a non-periodic kind and the single-pass walk with records for every step (NS_ERR_ARG
+     * otherwise).  With keep_last 1, min_ref 0, max_ref out of reach, min_steps = n_steps = K
+     * and prune_after 0, every walker follows a reversible trajectory of exactly K steps and
+     * returns its end point when inside, else its start point: an exact slice-sampling move
+     * (a refresh p <- a p + b e with a^2 + b^2 = 1 is an orthogonal map of (p, e), so the
+     * trajectory with the momentum flipped at its end is a measure-preserving involution),
+     * whereas a window that opens and closes on the walkers' reflection counts is not. */
     int midpoint;
 } ns_config;
 

@@ -246,10 +246,8 @@ ns_status validate(const ns_prior_box &b, const ns_likelihood_spec &lk, const ns
     }
     if (cfg.hss_mode < 0 || cfg.hss_mode > 2 || cfg.rec_len < 0 || cfg.noise_ahead < -1 || cfg.runs_per_group < 0)
         return fail(nullptr, NS_ERR_ARG, "launch choices out of range");
-    if (cfg.midpoint != 0 && (cfg.box_fold == 0 || cfg.noise_mode != 1 || cfg.keep_last != 0 ||
-                              lk.kind == NS_LIK_TORUS || cfg.hss_mode == 2))
-        return fail(nullptr, NS_ERR_ARG,
-                    "midpoint needs box_fold 1, noise_mode 1, keep_last 0, a non-periodic kind and the single pass");
+    if (cfg.midpoint != 0 && (cfg.box_fold == 0 || cfg.noise_mode != 1 || lk.kind == NS_LIK_TORUS || cfg.hss_mode == 2))
+        return fail(nullptr, NS_ERR_ARG, "midpoint needs box_fold 1, noise_mode 1, a non-periodic kind and the single pass");
     const int K = lk.n_comp;
     switch (lk.kind) {
     case NS_LIK_ISO_GAUSS:

@@ -52,8 +52,8 @@ def _agree(zg, zo, floor):
 
 
 # (name, configuration overrides): Appendix G's fixed step sizes, no momentum noise, the classic
-# termination, the fixed-step keep-last sampler, Algorithm 5's printed noise and pick, and the two
-# other readings of the prior box
+# termination, the fixed-step keep-last sampler, Algorithm 5's printed noise and pick, the two
+# other readings of the prior box, and the time-reversible step with its window or over a fixed length
 VARIANTS = [
     ("fixed dt 0.1", dict(dt_init=0.1, out_lo=0.0, out_hi=1.0)),
     ("fixed dt 0.5", dict(dt_init=0.5, out_lo=0.0, out_hi=1.0)),
@@ -65,6 +65,8 @@ VARIANTS = [
     ("exact box reflection", dict(box_fold=1)),
     ("exact box reflection, folds counted for dt", dict(box_fold=1, fold_counts=1)),
     ("time-reversible step", dict(box_fold=1, midpoint=1)),
+    ("time-reversible step, fixed length 20", dict(box_fold=1, midpoint=1, keep_last=1, n_steps=20, min_steps=20,
+                                                   min_ref=0, max_ref=10**6, prune_after=0)),
 ]
 
 
