@@ -8,17 +8,17 @@ likelihood evaluations.  With --midpoint the walk takes the time-reversible step
 oracle's midpoint option) instead of the printed one; --first N starts the run ids at N (new
 replicas beside earlier ones), --max-ref M runs that one trajectory length only, and --fixed K
 runs trajectories of exactly K steps that keep their last state (keep_last, min_ref 0, max_ref
-out of reach, no pruning) in place of the window.  Beside the offset each line gives the
+out of reach, no pruning) in place of the window; --delta-p X sets the refresh strength.  Beside the offset each line gives the
 fraction of walkers that returned their start point and the mean steps per walker.
 
-    python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8] [--first 0] [--max-ref 9 | --fixed 60]
+    python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8] [--first 0] [--max-ref 9 | --fixed 60] [--delta-p 0.5]
 """
 import math, multiprocessing as mp, os, sys, time
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import numpy as np
 
 def one(args):
-    d, n_live, mode, val, rid, mid = args
+    d, n_live, mode, val, rid, mid, dp = args
     import oracle
     from paper_2312_03911_gb300 import workloads as W
     rng = np.random.default_rng(W.SEED_BASE + 3)
@@ -29,7 +29,7 @@ def one(args):
         walk = dict(max_ref=val)
     else:
         walk = dict(keep_last=1, min_ref=0, max_ref=10**9, n_steps=val, min_steps=val, prune_after=0)
-    cfg = oracle.make_cfg(**dict(W.DEFAULT_CFG, n_live=n_live, clustering=0, seed=4242, run_id=rid, midpoint=mid,
+    cfg = oracle.make_cfg(**dict(W.DEFAULT_CFG, n_live=n_live, clustering=0, seed=4242, run_id=rid, midpoint=mid, delta_p=dp,
                                  **dict(W.BOX_FOLD, **walk)))
     r = oracle.run(lik, -np.ones(d), np.ones(d), cfg)
     truth = W.truth_logz(dict(name="x", spec=spec, lo=-np.ones(d), hi=np.ones(d), cfg={}))
@@ -42,6 +42,7 @@ def _arg(name, default):
 
 if __name__ == "__main__":
     import oracle; oracle.build()
+    from paper_2312_03911_gb300 import workloads as W
     d = int(sys.argv[1]) if len(sys.argv) > 1 else 32
     mid = int("--midpoint" in sys.argv)
     seeds, first = _arg("--seeds", 8), _arg("--first", 0)
@@ -51,14 +52,15 @@ if __name__ == "__main__":
         groups = [("max_ref", _arg("--max-ref", 0))]
     else:
         groups = [("max_ref", 3), ("max_ref", 9)]
-    jobs = [(d, 500, m, v, r, mid) for m, v in groups for r in range(first, first + seeds)]
+    dp = float(sys.argv[sys.argv.index("--delta-p") + 1]) if "--delta-p" in sys.argv else W.DEFAULT_CFG["delta_p"]
+    jobs = [(d, 500, m, v, r, mid, dp) for m, v in groups for r in range(first, first + seeds)]
     t0 = time.time()
     with mp.get_context("spawn").Pool(os.cpu_count()) as pool:
         res = pool.map(one, jobs, chunksize=1)
     for g in groups:
         rows = [x for x in res if x[0] == g]
         z = np.array([x[1] for x in rows])
-        print(f"d {d} {g[0]} {g[1]}: offset {z.mean():+.3f} +- {z.std(ddof=1)/math.sqrt(len(z)):.3f} "
+        print(f"d {d} {g[0]} {g[1]} delta_p {dp}: offset {z.mean():+.3f} +- {z.std(ddof=1)/math.sqrt(len(z)):.3f} "
               f"sd {z.std(ddof=1):.3f} stated {np.mean([x[2] for x in rows]):.3f} "
               f"n_like {np.mean([x[3] for x in rows]):.3g} start-point returns {np.mean([x[5] for x in rows]):.3f} "
               f"steps/walker {np.mean([x[6] for x in rows]):.1f} status {[x[4] for x in rows]}", flush=True)
