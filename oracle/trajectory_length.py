@@ -9,7 +9,9 @@ oracle's midpoint option) instead of the printed one; --first N starts the run i
 replicas beside earlier ones), --max-ref M runs that one trajectory length only, and --fixed K
 runs trajectories of exactly K steps that keep their last state (keep_last, min_ref 0, max_ref
 out of reach, no pruning) in place of the window; --delta-p X sets the refresh strength.  Beside the offset each line gives the
-fraction of walkers that returned their start point and the mean steps per walker.
+fraction of walkers that returned their start point (the oracle's fallback count: with the
+reversible step every start-point return, with the printed step only the walkers whose window
+saved nothing) and the mean steps per walker.
 
     python oracle/trajectory_length.py 128 [--midpoint] [--seeds 8] [--first 0] [--max-ref 9 | --fixed 60] [--delta-p 0.5]
 """
@@ -62,7 +64,7 @@ if __name__ == "__main__":
         z = np.array([x[1] for x in rows])
         print(f"d {d} {g[0]} {g[1]} delta_p {dp}: offset {z.mean():+.3f} +- {z.std(ddof=1)/math.sqrt(len(z)):.3f} "
               f"sd {z.std(ddof=1):.3f} stated {np.mean([x[2] for x in rows]):.3f} "
-              f"n_like {np.mean([x[3] for x in rows]):.3g} start-point returns {np.mean([x[5] for x in rows]):.3f} "
+              f"n_like {np.mean([x[3] for x in rows]):.3g} fallback {np.mean([x[5] for x in rows]):.3f} "
               f"steps/walker {np.mean([x[6] for x in rows]):.1f} status {[x[4] for x in rows]}", flush=True)
         print("  per run:", " ".join(f"{v:+.3f}" for v in z), flush=True)
     print("took", time.time() - t0)
